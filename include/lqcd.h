@@ -1,0 +1,193 @@
+/*
+ * lqcd.h -- C ABI of the GB300 (sm_103a) Incremental eigBiCG library.
+ *
+ * Method: A. Abdel-Rehim, K. Orginos, A. Stathopoulos, "Extending the eigCG
+ * algorithm to non-symmetric linear systems with multiple right-hand sides"
+ * (Lattice 2009, arXiv:0911.2285).  The library solves the paper's problem
+ * (Sec. 1, Eq. main-problem)
+ *
+ *     A x_i = b_i,   i = 1 .. N_r,
+ *
+ * for the Wilson-Dirac matrix A = 1 - kappa * D_hop of Sec. 3 (unpreconditioned,
+ * periodic boundaries), with two-sided Lanczos / BiCG (Sec. 2), the eigBiCG
+ * residual window and its BiCG-eigen restart (Algorithms eigBiCG and
+ * BiCG-eigen), and the incremental oblique deflation of later initial guesses
+ * (Algorithm Incremental eigBiCG).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice dims = {Lx, Ly, Lz, Lt}; site s = x + Lx*(y + Ly*(z + Lz*t)).
+ * Vectors ("fields") hold N = 12*V complex numbers, V = Lx*Ly*Lz*Lt, ordered
+ * [site][spin 4][colour 3], each complex as two doubles (re, im): a field is
+ * 24*V doubles.  Batches of k fields are k such arrays back to back.
+ * Links: [mu 4][site][3][3] complex128 (mu = 0..3 = x, y, z, t), row-major 3x3.
+ * D_hop psi(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                     + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu),
+ * gamma matrices Hermitian in the chiral basis, gamma5 = diag(1,1,-1,-1);
+ * A^+ = gamma5 A gamma5 (Sec. 4).
+ *
+ * Memory: the caller owns every buffer it passes.  With on_device = 0 the
+ * pointers are host memory (pageable or pinned); with on_device = 1 they are
+ * device pointers on the context's GPU, ordered on the context's stream.
+ * The context owns its device copies of the links, the residual windows and
+ * the accumulated eigenspace.
+ *
+ * Errors: every call returns lqcd_status; nothing throws across the ABI.  On a
+ * non-OK return, outputs are unspecified except the lqcd_solve_info entries,
+ * which are always written for every right-hand side that was started.
+ * The context stays usable after LQCD_ERR_NOCONV, LQCD_ERR_BREAKDOWN,
+ * LQCD_ERR_ARG and LQCD_ERR_STATE; after LQCD_ERR_CUDA or LQCD_ERR_OOM destroy it.
+ * Contexts are not thread safe: one host thread per context at a time.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LQCD_OK = 0,
+    LQCD_ERR_ARG = 1,        /* invalid argument or unsupported size */
+    LQCD_ERR_OOM = 2,        /* device allocation failed / over the HBM budget */
+    LQCD_ERR_CUDA = 3,       /* CUDA runtime error (message in lqcd_last_error) */
+    LQCD_ERR_NOCONV = 4,     /* maxiter reached before ||b - A x|| <= tol ||b|| */
+    LQCD_ERR_BREAKDOWN = 5,  /* BiCG breakdown: |rho| or |sigma| below 1e-14 of its scale */
+    LQCD_ERR_TIMEOUT = 6,    /* a bounded device wait gave up */
+    LQCD_ERR_STATE = 7       /* call not valid in this state (e.g. empty eigenspace) */
+} lqcd_status;
+
+typedef enum {
+    LQCD_FP64 = 0,   /* every vector and all arithmetic in FP64 */
+    LQCD_MIXED = 1   /* FP32 Krylov vectors/links (third-row reconstruction),
+                        FP64 solution, true residual and small dense algebra */
+} lqcd_precision;
+
+typedef enum {
+    LQCD_MODE_AUTO = 0,      /* eigBiCG until n1 sources have fed the eigenspace, then deflated */
+    LQCD_MODE_EIGBICG = 1,   /* Algorithm Incremental eigBiCG, phase 1 (deflate, eigBiCG, grow) */
+    LQCD_MODE_DEFLATED = 2,  /* phase 2: deflate the initial guess, then BiCG */
+    LQCD_MODE_PLAIN = 3      /* BiCG from the given initial guess, no deflation */
+} lqcd_mode;
+
+typedef struct {
+    int dims[4];              /* Lx, Ly, Lz, Lt; each >= 2 */
+    double kappa;             /* hopping parameter (Sec. 3: kappa = 1/(8 + 2 m_q)) */
+    int nev;                  /* Ritz pairs kept per restart / per solve (Sec. 2) */
+    int m;                    /* window size; must satisfy 2*nev < m <= 64 (Sec. 2: m > 2 nev) */
+    int n1;                   /* sources solved by eigBiCG before deflated solves (Alg. Incremental) */
+    double tol;               /* stop when ||b - A x|| <= tol ||b|| (FP64 true residual) */
+    int maxiter;              /* BiCG iterations per source */
+    lqcd_precision precision;
+    double deftol;            /* DefTol of Alg. Incremental; 0 disables the re-deflation restart */
+    int k_max;                /* right-hand sides per batched launch (1..8); 0 = 8 */
+    size_t hbm_budget_bytes;  /* 0 = no limit; init fails with LQCD_ERR_OOM above it */
+    int n_def_max;            /* eigenspace capacity in vectors (<= 80); 0 = min(80, n1*nev) */
+    double delta;             /* reliable-update trigger ||r|| < delta * max||r|| (MIXED); 0 = 0.1 */
+} lqcd_params;
+
+typedef struct {
+    int iters;               /* BiCG iterations */
+    int matvecs;             /* products with A or A^+ (the paper's cost unit, Sec. 3) */
+    int restarts;            /* BiCG-eigen restarts (eigBiCG mode) */
+    int reliable_updates;    /* FP64 true-residual recomputations */
+    int outer_steps;         /* DefTol re-deflation restarts */
+    double true_resid;       /* ||b - A x|| / ||b|| in FP64 at return */
+    double seconds;          /* wall time of this right-hand side's batch */
+    lqcd_mode mode_used;
+} lqcd_solve_info;
+
+typedef struct lqcd_ctx lqcd_ctx;
+
+/* Create a context for one gauge field and parameter set.
+ * links: host array [4][V][3][3] complex128 (interleaved doubles); copied.
+ * cuda_stream: cudaStream_t to order all work on, or NULL for a private stream.
+ * Allocates the device links (FP64 and, for MIXED, FP32 two-row), the batch
+ * slots (k_max) and the eigenspace (n_def_max).  Returns LQCD_ERR_ARG for bad
+ * dims/kappa/nev/m, LQCD_ERR_OOM when the device memory (or hbm_budget_bytes)
+ * is insufficient.  Sec. 2 (m > 2 nev), Sec. 3 (operator). */
+lqcd_status lqcd_eigbicg_init(lqcd_ctx **ctx, const lqcd_params *params,
+                              const double *links, void *cuda_stream);
+
+/* Solve A x_i = b_i for k right-hand sides (Sec. 1, Eq. main-problem).
+ * b: k fields; x: k fields, in = initial guesses (zeros allowed), out = solutions.
+ * mode: see lqcd_mode.  EIGBICG: each source is deflated against the current
+ * eigenspace, solved by eigBiCG(nev, m) and its nev Ritz pairs are
+ * bi-orthogonalized against the eigenspace and appended (Alg. Incremental,
+ * phase 1).  When k > 1 all k deflate against the eigenspace as it was at the
+ * call and append in index order at the end.  DEFLATED: deflate, BiCG, and with
+ * deftol > 0 one re-deflation restart at ||r|| < deftol ||b|| (phase 2).
+ * info: k entries (may be NULL).  k may exceed k_max: the sources are then
+ * processed in batches of k_max (continuous refill of freed slots).
+ * Returns LQCD_ERR_NOCONV / LQCD_ERR_BREAKDOWN if any source failed; x then
+ * holds the best iterate. */
+lqcd_status lqcd_solve(lqcd_ctx *ctx, int k, const double *b, double *x,
+                       int on_device, lqcd_mode mode, lqcd_solve_info *info);
+
+/* Oblique deflation of k initial guesses (Alg. Incremental, steps 2 and 3):
+ * x0 <- x0 + U_r d,  with  H d = U_l^+ (b - A x0),  H = U_l^+ A U_r.
+ * LQCD_ERR_STATE if the eigenspace is empty. */
+lqcd_status lqcd_deflate(lqcd_ctx *ctx, int k, const double *b, double *x0, int on_device);
+
+/* Eigenpairs of A from Rayleigh-Ritz on the accumulated spaces (Sec. 2, last
+ * paragraph): the pencil (U_l^+ A U_r, U_l^+ U_r).  *n_inout: in = capacity of
+ * the outputs, out = pairs written (<= eigenspace size), smallest |lambda| first.
+ * evals: n complex (2n doubles).  evecs_r, evecs_l: n host fields each or NULL.
+ * resid: n doubles ||A u - lambda u|| / ||u|| or NULL.  Host pointers only.
+ * LQCD_ERR_STATE if the eigenspace is empty. */
+lqcd_status lqcd_eigs(lqcd_ctx *ctx, int *n_inout, double *evals,
+                      double *evecs_r, double *evecs_l, double *resid);
+
+/* out = A in (dagger = 0) or A^+ in (dagger = 1), in the precision given
+ * (LQCD_FP64 or LQCD_MIXED = FP32 operator on FP32-rounded input).  k fields. */
+lqcd_status lqcd_apply(lqcd_ctx *ctx, int dagger, lqcd_precision prec, int k,
+                       const double *in, double *out, int on_device);
+
+/* Size of the eigenspace (number of right/left vector pairs). */
+int lqcd_eigspace_size(const lqcd_ctx *ctx);
+
+/* Copy the eigenspace out (checkpoint): Ur, Ul host fields (n each, may be
+ * NULL), H = U_l^+ A U_r as n x n complex row-major (may be NULL). */
+lqcd_status lqcd_eigspace_get(lqcd_ctx *ctx, double *Ur, double *Ul, double *H);
+
+/* Replace the eigenspace (resume / tests): n pairs of host fields; H is
+ * recomputed on the device as U_l^+ A U_r in FP64 and factorised.
+ * n = 0 empties it.  LQCD_ERR_ARG if n > n_def_max. */
+lqcd_status lqcd_eigspace_set(lqcd_ctx *ctx, int n, const double *Ur, const double *Ul);
+
+/* Inspect the eigBiCG window of the most recent eigBiCG solve (batch slot
+ * 'slot'): *vs = vectors in the window, H = vs x vs complex row-major (capacity
+ * m*m), ritz = its nev final Ritz values (complex, may be NULL), restarts. */
+lqcd_status lqcd_last_window(lqcd_ctx *ctx, int slot, int *vs, double *H,
+                             double *ritz, int *restarts);
+
+/* Device eigensolver for small dense complex matrices, exposed for tests:
+ * C is n x n complex row-major (host), n <= 80.  Returns all eigenvalues
+ * (smallest |lambda| first, exact ties by Im), right vectors Y (column j of an
+ * n x n row-major array, unit 2-norm, largest-modulus entry real > 0) and left
+ * vectors Z (Z^H Y = I on the diagonal).  Y, Z may be NULL. */
+lqcd_status lqcd_small_eig(int n, const double *C, double *evals, double *Y, double *Z);
+
+/* Coefficient part of Algorithm BiCG-eigen on the device, exposed for tests:
+ * H is m x m complex row-major (host).  Outputs *r (vectors kept, <= 2 nev),
+ * Yc, Zc (m x r row-major complex, capacity m*2nev) and lam (r complex). */
+lqcd_status lqcd_restart_coefficients(int m, int nev, const double *H, int *r,
+                                      double *Yc, double *Zc, double *lam);
+
+/* Text for a status code. */
+const char *lqcd_status_str(lqcd_status s);
+
+/* Last error message recorded by this thread (CUDA error text etc.). */
+const char *lqcd_last_error(void);
+
+/* Release every device resource of the context. NULL is accepted. */
+void lqcd_destroy(lqcd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQCD_H */

@@ -1,0 +1,153 @@
+// Wilson hopping term D_hop on one site, both precisions, and its adjoint.
+//
+//   D_hop psi(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu)
+//   D_hop^+ psi(x) = sum_mu (1 + gamma_mu) U_mu(x) psi(x+mu) + (1 - gamma_mu) U_mu(x-mu)^+ psi(x-mu)
+//
+// (the operator of the paper's test problems, Sec. 3; the adjoint follows from
+// gamma5 (1 -+ gamma_mu) gamma5 = (1 +- gamma_mu), Sec. 4).
+//
+// Chiral basis: gamma_mu = [[0, M_mu], [M_mu^+, 0]] with M_k = -i sigma_k, M_4 = 1.
+// For a sign sg = +-1, (1 + sg gamma_mu) psi = (h, sg M^+ h) with
+// h = psi_up + sg M psi_lo (two spin components of three colours), so each
+// hop multiplies only the half spinor h by the link and rebuilds the lower
+// half with sign/i permutations (no multiplications).
+#pragma once
+#include "common.cuh"
+
+namespace lqcd {
+
+struct LinksD {   // FP64, all 18 reals
+    const double2* u;
+    int V;
+    __device__ __forceinline__ void load(int mu, int s, double2 (&m)[3][3]) const {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) m[e / 3][e % 3] = __ldg(u + (size_t)(mu * 9 + e) * V + s);
+    }
+};
+
+struct LinksF {   // FP32 rows 0, 1; row 2 rebuilt as conj(row0 x row1)
+    const float4* u;
+    int V;
+    __device__ __forceinline__ void load(int mu, int s, float2 (&m)[3][3]) const {
+        float4 a = __ldg(u + (size_t)(mu * 3 + 0) * V + s);
+        float4 b = __ldg(u + (size_t)(mu * 3 + 1) * V + s);
+        float4 c = __ldg(u + (size_t)(mu * 3 + 2) * V + s);
+        m[0][0] = make_float2(a.x, a.y); m[0][1] = make_float2(a.z, a.w);
+        m[0][2] = make_float2(b.x, b.y); m[1][0] = make_float2(b.z, b.w);
+        m[1][1] = make_float2(c.x, c.y); m[1][2] = make_float2(c.z, c.w);
+        m[2][0] = conj_(m[0][1] * m[1][2] - m[0][2] * m[1][1]);
+        m[2][1] = conj_(m[0][2] * m[1][0] - m[0][0] * m[1][2]);
+        m[2][2] = conj_(m[0][0] * m[1][1] - m[0][1] * m[1][0]);
+    }
+};
+
+template <typename T> struct LinkSel;
+template <> struct LinkSel<float> { using type = LinksF; };
+template <> struct LinkSel<double> { using type = LinksD; };
+
+// h_a = psi_a + sg (M_mu psi_lo)_a, a = 0, 1; psi index = spin*3 + colour.
+template <int MU, int SG, typename C>
+__device__ __forceinline__ void project(const C (&psi)[12], C (&h)[2][3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        C p0 = psi[c], p1 = psi[3 + c], p2 = psi[6 + c], p3 = psi[9 + c];
+        C m0, m1;
+        if (MU == 0) { m0 = mul_mi(p3); m1 = mul_mi(p2); }
+        else if (MU == 1) { m0 = -p3; m1 = p2; }
+        else if (MU == 2) { m0 = mul_mi(p2); m1 = mul_i(p3); }
+        else { m0 = p2; m1 = p3; }
+        if (SG > 0) { h[0][c] = p0 + m0; h[1][c] = p1 + m1; }
+        else { h[0][c] = p0 - m0; h[1][c] = p1 - m1; }
+    }
+}
+
+// acc += (uh, sg M_mu^+ uh)
+template <int MU, int SG, typename C>
+__device__ __forceinline__ void reconstruct(const C (&uh)[2][3], C (&acc)[12]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        C a = uh[0][c], b = uh[1][c];
+        C l0, l1;   // M^+ (a, b)
+        if (MU == 0) { l0 = mul_i(b); l1 = mul_i(a); }
+        else if (MU == 1) { l0 = b; l1 = -a; }
+        else if (MU == 2) { l0 = mul_i(a); l1 = mul_mi(b); }
+        else { l0 = a; l1 = b; }
+        acc[c] = acc[c] + a;
+        acc[3 + c] = acc[3 + c] + b;
+        if (SG > 0) { acc[6 + c] = acc[6 + c] + l0; acc[9 + c] = acc[9 + c] + l1; }
+        else { acc[6 + c] = acc[6 + c] - l0; acc[9 + c] = acc[9 + c] - l1; }
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void su3_mul(const C (&u)[3][3], const C (&h)[2][3], C (&o)[2][3]) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) o[a][r] = u[r][0] * h[a][0] + u[r][1] * h[a][1] + u[r][2] * h[a][2];
+}
+template <typename C>
+__device__ __forceinline__ void su3_dag_mul(const C (&u)[3][3], const C (&h)[2][3], C (&o)[2][3]) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) o[a][r] = cdot(u[0][r], h[a][0]) + cdot(u[1][r], h[a][1]) + cdot(u[2][r], h[a][2]);
+}
+
+// Input accessors: in.load(site, psi) fills 12 complex values.
+template <typename S> struct FieldIn {
+    const void* p;
+    int V;
+    template <typename C> __device__ __forceinline__ void load(int s, C (&v)[12]) const { Field<S>::load(p, V, s, v); }
+};
+// x_hi (FP64) + x_lo (storage S), summed in FP64.
+template <typename S> struct SumIn {
+    const void* hi;
+    const void* lo;
+    int V;
+    __device__ __forceinline__ void load(int s, double2 (&v)[12]) const {
+        double2 a[12], b[12];
+        Field<double>::load(hi, V, s, a);
+        Field<S>::load(lo, V, s, b);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) v[c] = a[c] + b[c];
+    }
+};
+
+template <int MU, bool DAG, typename T, class LK, class IN>
+__device__ __forceinline__ void hop_dir(const Geom& g, const LK& U, const IN& in, int s,
+                                        cplx<T> (&acc)[12]) {
+    using C = cplx<T>;
+    constexpr int SF = DAG ? +1 : -1;   // forward projector sign
+    C psi[12], h[2][3], uh[2][3], u[3][3];
+    {
+        int sf = g.fwd(s, MU);
+        in.load(sf, psi);
+        project<MU, SF>(psi, h);
+        U.load(MU, s, u);
+        su3_mul(u, h, uh);
+        reconstruct<MU, SF>(uh, acc);
+    }
+    {
+        int sb = g.bwd(s, MU);
+        in.load(sb, psi);
+        project<MU, -SF>(psi, h);
+        U.load(MU, sb, u);
+        su3_dag_mul(u, h, uh);
+        reconstruct<MU, -SF>(uh, acc);
+    }
+}
+
+// acc = D_hop psi (DAG = false) or D_hop^+ psi (DAG = true) at site s.
+template <bool DAG, typename T, class LK, class IN>
+__device__ __forceinline__ void hop_site(const Geom& g, const LK& U, const IN& in, int s,
+                                         cplx<T> (&acc)[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = mk<T>(T(0), T(0));
+    hop_dir<0, DAG, T>(g, U, in, s, acc);
+    hop_dir<1, DAG, T>(g, U, in, s, acc);
+    hop_dir<2, DAG, T>(g, U, in, s, acc);
+    hop_dir<3, DAG, T>(g, U, in, s, acc);
+}
+
+}  // namespace lqcd

@@ -1,0 +1,718 @@
+// Small dense FP64 complex algebra on the device, one CTA per problem:
+//  * eig with right and left eigenvectors ([zr, zl, D] = eig(C), paper Sec. 1
+//    notation), eigenvalues ordered by smallest |lambda| (Sec. 2);
+//  * the coefficient-space part of Algorithm BiCG-eigen (Sec. 2);
+//  * final Ritz pairs of an eigBiCG window (Algorithm eigBiCG, step 4);
+//  * LU factorisation / solves for H = U_l^H A U_r (Algorithm Incremental).
+//
+// Eigen-solver: Householder reduction to Hessenberg form, complex single-shift
+// (Wilkinson) implicit QR to Schur form T = Q^H C Q (Golub & Van Loan,
+// "Matrix Computations", Sec. 7.4-7.5), eigenvectors of T by back / forward
+// substitution, mapped back with Q. Conventions: right vectors have unit
+// 2-norm with their largest-modulus entry real positive; left vectors satisfy
+// z^H y = 1.
+#include "kernels.cuh"
+
+namespace lqcd {
+namespace {
+
+constexpr int ET = 128;          // threads per eigen CTA
+constexpr double EPS = 2.220446049250313e-16;
+
+__device__ __forceinline__ double2 czero() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double2 cone() { return make_double2(1.0, 0.0); }
+
+// Givens G = [[c, s], [-conj(s), c]] with G [x; y] = [r; 0].
+__device__ __forceinline__ void givens(double2 x, double2 y, double& c, double2& s) {
+    double ax = cabs_(x), ay = cabs_(y);
+    if (ay == 0.0) { c = 1.0; s = czero(); return; }
+    if (ax == 0.0) { c = 0.0; s = cone(); return; }
+    double nrm = hypot(ax, ay);
+    c = ax / nrm;
+    double2 ph = make_double2(x.x / ax, x.y / ax);
+    s = (1.0 / nrm) * (ph * conj_(y));
+}
+
+// ---------------------------------------------------------------------------
+// Block-cooperative eigen-solver on A (n x n, leading dim lda, shared memory).
+// On return A holds the Schur form T, Q the Schur vectors. Returns 0 on
+// success, 1 if QR failed to converge.
+__device__ int schur(double2* A, double2* Q, int n, int lda, double2* v /* n */, double* sh) {
+    const int tid = threadIdx.x;
+    // Q = I
+    for (int e = tid; e < n * lda; e += blockDim.x) Q[e] = ((e / lda) == (e % lda)) ? cone() : czero();
+    __syncthreads();
+    // Householder reduction to upper Hessenberg.
+    for (int k = 0; k + 2 < n; ++k) {
+        // v = x + e^{i theta} ||x|| e1, x = A[k+1:n, k]
+        if (tid == 0) {
+            double nrm2 = 0.0;
+            for (int i = k + 1; i < n; ++i) nrm2 += cabs2(A[i * lda + k]);
+            double alpha = sqrt(nrm2);
+            double2 x0 = A[(k + 1) * lda + k];
+            double ax0 = cabs_(x0);
+            double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : cone();
+            sh[0] = alpha;
+            sh[1] = alpha > 0.0 ? 1.0 / (alpha * (alpha + ax0)) : 0.0;   // tau = 2/||v||^2
+            sh[2] = ph.x; sh[3] = ph.y;
+        }
+        __syncthreads();
+        double alpha = sh[0], tau = sh[1];
+        double2 ph = make_double2(sh[2], sh[3]);
+        if (alpha == 0.0) { __syncthreads(); continue; }
+        for (int i = k + 1 + tid; i < n; i += blockDim.x) v[i - k - 1] = A[i * lda + k];
+        __syncthreads();
+        if (tid == 0) v[0] = v[0] + alpha * ph;
+        __syncthreads();
+        const int len = n - k - 1;
+        // rows k+1..n-1 of A: A -= tau v (v^H A), columns k..n-1
+        for (int j = k + tid; j < n; j += blockDim.x) {
+            double2 w = czero();
+            for (int i = 0; i < len; ++i) w = w + cdot(v[i], A[(k + 1 + i) * lda + j]);
+            w = tau * w;
+            for (int i = 0; i < len; ++i) A[(k + 1 + i) * lda + j] = A[(k + 1 + i) * lda + j] - v[i] * w;
+        }
+        __syncthreads();
+        // columns k+1..n-1 of A (all rows) and of Q: X -= tau (X v) v^H
+        for (int i = tid; i < 2 * n; i += blockDim.x) {
+            double2* row = i < n ? A + i * lda : Q + (i - n) * lda;
+            double2 u = czero();
+            for (int l = 0; l < len; ++l) u = u + row[k + 1 + l] * v[l];
+            u = tau * u;
+            for (int l = 0; l < len; ++l) row[k + 1 + l] = row[k + 1 + l] - mulc(u, v[l]);
+        }
+        __syncthreads();
+        for (int i = k + 2 + tid; i < n; i += blockDim.x) A[i * lda + k] = czero();
+        __syncthreads();
+    }
+    // Frobenius norm for the negligibility tests.
+    if (tid == 0) {
+        double f = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = (i > 0 ? i - 1 : 0); j < n; ++j) f += cabs2(A[i * lda + j]);
+        sh[4] = sqrt(f);
+    }
+    __syncthreads();
+    const double anorm = sh[4] > 0.0 ? sh[4] : 1.0;
+    // Single-shift implicit QR with deflation from the bottom.
+    __shared__ int s_l, s_hi, s_fail;
+    __shared__ double s_c;
+    __shared__ double2 s_s, s_mu;
+    if (tid == 0) { s_hi = n - 1; s_fail = 0; }
+    __syncthreads();
+    int iters = 0, total = 0;
+    while (true) {
+        if (tid == 0) {
+            int hi = s_hi;
+            int l = hi;
+            while (l > 0) {
+                double tst = cabs_(A[(l - 1) * lda + l - 1]) + cabs_(A[l * lda + l]);
+                if (tst == 0.0) tst = anorm;
+                if (cabs_(A[l * lda + l - 1]) <= EPS * tst) { A[l * lda + l - 1] = czero(); break; }
+                --l;
+            }
+            s_l = l;
+        }
+        __syncthreads();
+        int hi = s_hi, l = s_l;
+        if (hi <= 0) break;
+        if (l == hi) {
+            __syncthreads();
+            if (tid == 0) s_hi = hi - 1;
+            iters = 0;
+            __syncthreads();
+            continue;
+        }
+        ++iters; ++total;
+        if (iters > 60 || total > 60 * n) { if (tid == 0) s_fail = 1; __syncthreads(); break; }
+        if (tid == 0) {
+            double2 a = A[(hi - 1) * lda + hi - 1], b = A[(hi - 1) * lda + hi];
+            double2 c = A[hi * lda + hi - 1], d = A[hi * lda + hi];
+            double2 mu;
+            if (iters % 11 == 10) {
+                // exceptional shift
+                mu = d + make_double2(0.75 * cabs_(c), 0.0);
+            } else {
+                double2 t = 0.5 * (a - d);
+                double2 bc = b * c;
+                double2 disc2 = t * t + bc;
+                // complex sqrt
+                double r = cabs_(disc2);
+                double sx = sqrt(0.5 * (r + disc2.x));
+                double sy = sqrt(0.5 * (r - disc2.x));
+                if (disc2.y < 0) sy = -sy;
+                double2 disc = make_double2(sx, sy);
+                double2 den1 = t + disc, den2 = t - disc;
+                double2 den = cabs2(den1) >= cabs2(den2) ? den1 : den2;
+                mu = cabs2(den) > 0.0 ? d - cdiv(bc, den) : d;
+            }
+            s_mu = mu;
+        }
+        __syncthreads();
+        double2 mu = s_mu;
+        for (int k = l; k < hi; ++k) {
+            if (tid == 0) {
+                double2 x, y;
+                if (k == l) { x = A[l * lda + l] - mu; y = A[(l + 1) * lda + l]; }
+                else { x = A[k * lda + k - 1]; y = A[(k + 1) * lda + k - 1]; }
+                double c; double2 s;
+                givens(x, y, c, s);
+                s_c = c; s_s = s;
+            }
+            __syncthreads();
+            const double c = s_c;
+            const double2 s = s_s;
+            // rows k, k+1
+            const int j0 = (k == l) ? l : k - 1;
+            for (int j = j0 + tid; j < n; j += blockDim.x) {
+                double2 a = A[k * lda + j], b = A[(k + 1) * lda + j];
+                A[k * lda + j] = c * a + s * b;
+                A[(k + 1) * lda + j] = c * b - conj_(s) * a;
+            }
+            __syncthreads();
+            // columns k, k+1 of A (rows 0..min(k+2, hi)) and of Q (all rows)
+            const int i1 = min(k + 2, hi);
+            for (int i = tid; i < (i1 + 1) + n; i += blockDim.x) {
+                double2* row = i <= i1 ? A + i * lda : Q + (i - i1 - 1) * lda;
+                double2 a = row[k], b = row[k + 1];
+                row[k] = c * a + conj_(s) * b;
+                row[k + 1] = c * b - s * a;
+            }
+            __syncthreads();
+            if (k > l && tid == 0) A[(k + 1) * lda + k - 1] = czero();
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    int fail = s_fail;
+    __syncthreads();
+    return fail;
+}
+
+// Order of the eigenvalues on the diagonal of T: smallest |lambda|, then Im.
+__device__ void order_eigs(const double2* T, int n, int lda, int* ord) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n; ++i) ord[i] = i;
+        for (int i = 1; i < n; ++i) {
+            int key = ord[i];
+            double2 lk = T[key * lda + key];
+            double ak = cabs_(lk);
+            int j = i - 1;
+            while (j >= 0) {
+                double2 lj = T[ord[j] * lda + ord[j]];
+                double aj = cabs_(lj);
+                bool after = (aj > ak) || (aj == ak && lj.y > lk.y);
+                if (!after) break;
+                ord[j + 1] = ord[j];
+                --j;
+            }
+            ord[j + 1] = key;
+        }
+    }
+    __syncthreads();
+}
+
+// Eigenvectors for the eigenvalues T[ord[i], ord[i]], i < nsel.
+// Y, Z (global or shared), column i of an n x nsel row-major array (ld = ldyz).
+// W1, W2: scratch of n*nsel each (y', w in Schur coordinates).
+__device__ void eigvecs(const double2* T, const double2* Q, int n, int lda, const int* ord, int nsel,
+                        double2* Y, double2* Z, int ldyz, double2* W1, double2* W2, double anorm) {
+    const int tid = threadIdx.x;
+    const double smin = fmax(EPS * anorm, 1e-300);
+    // Back / forward substitution, one (vector, side) per thread.
+    for (int t = tid; t < 2 * nsel; t += blockDim.x) {
+        const int i = t % nsel;
+        const bool left = t >= nsel;
+        const int k = ord[i];
+        const double2 lam = T[k * lda + k];
+        double2* w = (left ? W2 : W1) + (size_t)i * n;
+        for (int j = 0; j < n; ++j) w[j] = czero();
+        w[k] = cone();
+        if (!left) {
+            for (int j = k - 1; j >= 0; --j) {
+                double2 sacc = czero();
+                for (int l = j + 1; l <= k; ++l) sacc = sacc + T[j * lda + l] * w[l];
+                double2 d = T[j * lda + j] - lam;
+                if (cabs_(d) < smin) d = make_double2(smin, 0.0);
+                w[j] = -cdiv(sacc, d);
+                if (cabs_(w[j]) > 1e150) {
+                    for (int l = j; l <= k; ++l) w[l] = 1e-150 * w[l];
+                }
+            }
+        } else {
+            for (int j = k + 1; j < n; ++j) {
+                double2 sacc = czero();
+                for (int l = k; l < j; ++l) sacc = sacc + w[l] * T[l * lda + j];
+                double2 d = T[j * lda + j] - lam;
+                if (cabs_(d) < smin) d = make_double2(smin, 0.0);
+                w[j] = -cdiv(sacc, d);
+                if (cabs_(w[j]) > 1e150) {
+                    for (int l = k; l <= j; ++l) w[l] = 1e-150 * w[l];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // Y = Q y', Z = Q conj(w)
+    for (int e = tid; e < 2 * n * nsel; e += blockDim.x) {
+        const bool left = e >= n * nsel;
+        const int ee = left ? e - n * nsel : e;
+        const int row = ee / nsel, i = ee % nsel;
+        const double2* w = (left ? W2 : W1) + (size_t)i * n;
+        double2 acc = czero();
+        for (int l = 0; l < n; ++l) acc = acc + Q[row * lda + l] * (left ? conj_(w[l]) : w[l]);
+        (left ? Z : Y)[row * ldyz + i] = acc;
+    }
+    __syncthreads();
+    // Normalise: ||y|| = 1, largest entry real positive, z^H y = 1.
+    for (int i = tid; i < nsel; i += blockDim.x) {
+        double nrm2 = 0.0, best = -1.0;
+        int arg = 0;
+        for (int r = 0; r < n; ++r) {
+            double a2 = cabs2(Y[r * ldyz + i]);
+            nrm2 += a2;
+            if (a2 > best) { best = a2; arg = r; }
+        }
+        double nrm = sqrt(nrm2);
+        double2 pk = Y[arg * ldyz + i];
+        double apk = cabs_(pk);
+        // factor = conj(pk)/|pk| / nrm
+        double2 f = (apk > 0.0 && nrm > 0.0) ? (1.0 / (apk * nrm)) * conj_(pk) : make_double2(nrm > 0.0 ? 1.0 / nrm : 1.0, 0.0);
+        double2 d = czero();
+        for (int r = 0; r < n; ++r) {
+            double2 yv = f * Y[r * ldyz + i];
+            Y[r * ldyz + i] = yv;
+            d = d + cdot(Z[r * ldyz + i], yv);
+        }
+        double2 g = cabs2(d) > 0.0 ? cdiv(cone(), conj_(d)) : cone();
+        for (int r = 0; r < n; ++r) Z[r * ldyz + i] = g * Z[r * ldyz + i];
+    }
+    __syncthreads();
+}
+
+// Full eigen-solve of the n x n matrix in A (shared). Outputs sorted
+// eigenvalues to lam (n), and vectors for the first nsel.
+__device__ int eig_block(double2* A, double2* Q, int n, int lda, int nsel, double2* lam, double2* Y,
+                         double2* Z, int ldyz, double2* W1, double2* W2, double2* v, double* sh, int* ord) {
+    int fail = schur(A, Q, n, lda, v, sh);
+    double anorm = sh[4];
+    order_eigs(A, n, lda, ord);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = A[ord[i] * lda + ord[i]];
+    __syncthreads();
+    if (nsel > 0) eigvecs(A, Q, n, lda, ord, nsel, Y, Z, ldyz, W1, W2, anorm);
+    return fail;
+}
+
+// Dynamic shared memory layout for an eigen CTA of capacity nmax.
+struct EigSmem {
+    double2* A; double2* Q; double2* v; double* sh; int* ord;
+    __device__ EigSmem(char* base, int nmax) {
+        A = reinterpret_cast<double2*>(base);
+        Q = A + nmax * nmax;
+        v = Q + nmax * nmax;
+        sh = reinterpret_cast<double*>(v + nmax);
+        ord = reinterpret_cast<int*>(sh + 8);
+    }
+    static size_t bytes(int nmax) {
+        return (size_t)(2 * nmax * nmax + nmax) * sizeof(double2) + 8 * sizeof(double) + nmax * sizeof(int) + 16;
+    }
+};
+
+__global__ void __launch_bounds__(ET) small_eig_kernel(int n, const double2* Ain, int lda_in, int nsel,
+                                                       double2* lam, double2* Y, double2* Z, int ldyz,
+                                                       double2* W, int* info) {
+    extern __shared__ __align__(16) char smem[];
+    EigSmem S(smem, n);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) S.A[e] = Ain[(e / n) * lda_in + (e % n)];
+    __syncthreads();
+    int fail = eig_block(S.A, S.Q, n, n, nsel, lam, Y, Z, ldyz, W, W + (size_t)n * max(nsel, 1), S.v, S.sh, S.ord);
+    if (threadIdx.x == 0 && info) *info = fail;
+}
+
+// ------------------------------------------------------- BiCG-eigen (coeffs)
+// Work arrays (global, per problem) for the restart coefficient computation.
+struct RestartWork {
+    double2 *y1, *z1, *y2, *z2, *HY, *T, *u, *q, *W1, *W2, *lamtmp, *M;
+    int *rowp, *colp;
+    static size_t elems(int m, int nev) {
+        const int r = 2 * nev;
+        return (size_t)m * nev * 4 + (size_t)m * r + (size_t)r * r * 3 + (size_t)m * m * 2 + m + (size_t)nev * nev + 64;
+    }
+    __device__ RestartWork(double2* base, int m, int nev) {
+        const int r = 2 * nev;
+        y1 = base; z1 = y1 + m * nev; y2 = z1 + m * nev; z2 = y2 + m * nev;
+        HY = z2 + m * nev; T = HY + m * r; u = T + r * r; q = u + r * r;
+        W1 = q + r * r; W2 = W1 + m * m; lamtmp = W2 + m * m; M = lamtmp + m;
+        rowp = reinterpret_cast<int*>(M + nev * nev);
+        colp = rowp + 32;
+    }
+};
+
+// Algorithm BiCG-eigen in coefficient space for H (m x m, ld = ldh, global).
+// Writes Yc, Zc ((m) x r, ld = ldc), lam (r); returns r (0 on failure).
+__device__ int restart_coeffs_block(const double2* H, int ldh, int m, int nev, double2* Yc, double2* Zc,
+                                    int ldc, double2* lam, EigSmem& S, RestartWork& Wk, int* fail_out) {
+    const int tid = threadIdx.x;
+    int fail = 0;
+    // 1. eig(H^(m)), nev smallest: y1, z1 (m x nev)
+    for (int e = tid; e < m * m; e += blockDim.x) S.A[e] = H[(e / m) * ldh + (e % m)];
+    __syncthreads();
+    fail |= eig_block(S.A, S.Q, m, m, nev, Wk.lamtmp, Wk.y1, Wk.z1, nev, Wk.W1, Wk.W2, S.v, S.sh, S.ord);
+    // 2. eig(H^(m-1)), nev smallest, padded with a zero row: y2, z2 (m x nev)
+    const int m1 = m - 1;
+    for (int e = tid; e < m1 * m1; e += blockDim.x) S.A[e] = H[(e / m1) * ldh + (e % m1)];
+    __syncthreads();
+    fail |= eig_block(S.A, S.Q, m1, m1, nev, Wk.lamtmp, Wk.y2, Wk.z2, nev, Wk.W1, Wk.W2, S.v, S.sh, S.ord);
+    for (int i = tid; i < nev; i += blockDim.x) { Wk.y2[m1 * nev + i] = czero(); Wk.z2[m1 * nev + i] = czero(); }
+    __syncthreads();
+    // 3. y2 -= y1 (z1^H y2), z2 -= z1 (y1^H z2)   (coefficients in S.A as scratch)
+    double2* G1 = S.A;                 // nev x nev : z1^H y2
+    double2* G2 = S.A + nev * nev;     // nev x nev : y1^H z2
+    for (int e = tid; e < 2 * nev * nev; e += blockDim.x) {
+        const bool second = e >= nev * nev;
+        const int ee = second ? e - nev * nev : e;
+        const int i = ee / nev, j = ee % nev;
+        const double2* L = second ? Wk.y1 : Wk.z1;
+        const double2* R = second ? Wk.z2 : Wk.y2;
+        double2 acc = czero();
+        for (int r = 0; r < m; ++r) acc = acc + cdot(L[r * nev + i], R[r * nev + j]);
+        (second ? G2 : G1)[i * nev + j] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < 2 * m * nev; e += blockDim.x) {
+        const bool second = e >= m * nev;
+        const int ee = second ? e - m * nev : e;
+        const int r = ee / nev, j = ee % nev;
+        const double2* B = second ? Wk.z1 : Wk.y1;
+        const double2* G = second ? G2 : G1;
+        double2 acc = czero();
+        for (int i = 0; i < nev; ++i) acc = acc + B[r * nev + i] * G[i * nev + j];
+        double2* X = second ? Wk.z2 : Wk.y2;
+        X[r * nev + j] = X[r * nev + j] - acc;
+    }
+    __syncthreads();
+    // 4. M = z2^H y2, LU with complete pivoting (thread 0), rank by pivot >= 1e-10
+    for (int e = tid; e < nev * nev; e += blockDim.x) {
+        const int i = e / nev, j = e % nev;
+        double2 acc = czero();
+        for (int r = 0; r < m; ++r) acc = acc + cdot(Wk.z2[r * nev + i], Wk.y2[r * nev + j]);
+        Wk.M[i * nev + j] = acc;
+    }
+    __syncthreads();
+    __shared__ int s_rank;
+    if (tid == 0) {
+        double2* a = Wk.M;
+        int rank = 0;
+        for (int i = 0; i < nev; ++i) { Wk.rowp[i] = i; Wk.colp[i] = i; }
+        for (int i = 0; i < nev; ++i) {
+            double best = -1.0; int pr = i, pc = i;
+            for (int r = i; r < nev; ++r)
+                for (int c = i; c < nev; ++c) {
+                    double v = cabs_(a[r * nev + c]);
+                    if (v > best) { best = v; pr = r; pc = c; }
+                }
+            if (best < 1e-10) break;
+            if (pr != i) {
+                for (int c = 0; c < nev; ++c) { double2 t = a[i * nev + c]; a[i * nev + c] = a[pr * nev + c]; a[pr * nev + c] = t; }
+                int t = Wk.rowp[i]; Wk.rowp[i] = Wk.rowp[pr]; Wk.rowp[pr] = t;
+            }
+            if (pc != i) {
+                for (int r = 0; r < nev; ++r) { double2 t = a[r * nev + i]; a[r * nev + i] = a[r * nev + pc]; a[r * nev + pc] = t; }
+                int t = Wk.colp[i]; Wk.colp[i] = Wk.colp[pc]; Wk.colp[pc] = t;
+            }
+            for (int r = i + 1; r < nev; ++r) a[r * nev + i] = cdiv(a[r * nev + i], a[i * nev + i]);
+            for (int r = i + 1; r < nev; ++r)
+                for (int c = i + 1; c < nev; ++c) a[r * nev + c] = a[r * nev + c] - a[r * nev + i] * a[i * nev + c];
+            ++rank;
+        }
+        s_rank = rank;
+    }
+    __syncthreads();
+    const int rank = s_rank;
+    const int r = nev + rank;
+    // 5. yt = [y1, y2(:,colp) U^{-1}], zt = [z1, z2(:,rowp) L^{-H}]  (in HY/W1 as m x r arrays)
+    double2* yt = Wk.W1;   // m x r (ld r)
+    double2* zt = Wk.W2;
+    for (int e = tid; e < m * nev; e += blockDim.x) {
+        const int row = e / nev, i = e % nev;
+        yt[row * r + i] = Wk.y1[row * nev + i];
+        zt[row * r + i] = Wk.z1[row * nev + i];
+    }
+    for (int row = tid; row < 2 * m; row += blockDim.x) {
+        const bool zs = row >= m;
+        const int rr = zs ? row - m : row;
+        double2* out = (zs ? zt : yt) + rr * r + nev;
+        const double2* in = (zs ? Wk.z2 : Wk.y2) + rr * nev;
+        for (int j = 0; j < rank; ++j) {
+            double2 acc = in[zs ? Wk.rowp[j] : Wk.colp[j]];
+            for (int i = 0; i < j; ++i) {
+                if (!zs) acc = acc - out[i] * Wk.M[i * nev + j];            // U_{ij}
+                else acc = acc - out[i] * conj_(Wk.M[j * nev + i]);         // conj(L_{ji})
+            }
+            out[j] = zs ? acc : cdiv(acc, Wk.M[j * nev + j]);
+        }
+    }
+    __syncthreads();
+    // 6. T = zt^H H yt (r x r)
+    for (int e = tid; e < m * r; e += blockDim.x) {
+        const int row = e / r, j = e % r;
+        double2 acc = czero();
+        for (int l = 0; l < m; ++l) acc = acc + H[row * ldh + l] * yt[l * r + j];
+        Wk.HY[row * r + j] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < r * r; e += blockDim.x) {
+        const int i = e / r, j = e % r;
+        double2 acc = czero();
+        for (int l = 0; l < m; ++l) acc = acc + cdot(zt[l * r + i], Wk.HY[l * r + j]);
+        S.A[e] = acc;
+    }
+    __syncthreads();
+    // 7. eig(T): all r pairs -> u, q, lam
+    fail |= eig_block(S.A, S.Q, r, r, r, lam, Wk.u, Wk.q, r, Wk.T, Wk.HY, S.v, S.sh, S.ord);
+    // 8. Yc = yt u, Zc = zt q
+    for (int e = tid; e < 2 * m * r; e += blockDim.x) {
+        const bool zs = e >= m * r;
+        const int ee = zs ? e - m * r : e;
+        const int row = ee / r, j = ee % r;
+        const double2* X = zs ? zt : yt;
+        const double2* C = zs ? Wk.q : Wk.u;
+        double2 acc = czero();
+        for (int l = 0; l < r; ++l) acc = acc + X[row * r + l] * C[l * r + j];
+        (zs ? Zc : Yc)[row * ldc + j] = acc;
+    }
+    __syncthreads();
+    *fail_out = fail;
+    return r;
+}
+
+__global__ void __launch_bounds__(ET) restart_single_kernel(int m, int nev, const double2* H, int* r_out,
+                                                            double2* Yc, double2* Zc, double2* lam,
+                                                            double2* work, int* info) {
+    extern __shared__ __align__(16) char smem[];
+    EigSmem S(smem, m);
+    RestartWork Wk(work, m, nev);
+    int fail = 0;
+    int r = restart_coeffs_block(H, m, m, nev, Yc, Zc, 2 * nev, lam, S, Wk, &fail);
+    if (threadIdx.x == 0) { *r_out = r; *info = fail; }
+}
+
+// Restart of every slot whose window is full (vs == m): coefficients, H = diag(lam).
+__global__ void __launch_bounds__(ET) restart_slots_kernel(SlotState* states, const SlotPtrs* ptrs,
+                                                           double2* work_base, size_t work_stride) {
+    SlotState& st = states[blockIdx.x];
+    const SlotPtrs& P = ptrs[blockIdx.x];
+    __shared__ int go;
+    if (threadIdx.x == 0) {
+        go = (st.status == ST_RUNNING && st.m > 0 && st.vs == st.m);
+        if (!go) st.restart_r = 0;
+    }
+    __syncthreads();
+    if (!go) return;
+    extern __shared__ __align__(16) char smem[];
+    const int m = st.m, nev = st.nev;
+    EigSmem S(smem, m);
+    RestartWork Wk(work_base + work_stride * blockIdx.x, m, nev);
+    const int ldc = 2 * nev + 1;
+    int fail = 0;
+    int r = restart_coeffs_block(P.H, m, m, nev, P.coefY, P.coefZ, ldc, P.lam, S, Wk, &fail);
+    // H = diag(lam)
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        P.H[e] = (i == j && i < r) ? P.lam[i] : czero();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (fail) st.status = ST_BREAKDOWN;
+        st.restart_r = r;
+        st.vs = r;
+        st.restarts += 1;
+    }
+}
+
+// Final Ritz pairs of a window: eig(H^(vs)), nev smallest, scales folded.
+__global__ void __launch_bounds__(ET) final_ritz_kernel(SlotState* states, const SlotPtrs* ptrs, int slot,
+                                                        double2* Yc, double2* Zc, double2* lam, int* nout,
+                                                        double2* work) {
+    const SlotState& st = states[slot];
+    const SlotPtrs& P = ptrs[slot];
+    const int n = st.vs, m = st.m;
+    const int nsel = min(st.nev, n);
+    if (n == 0) { if (threadIdx.x == 0) *nout = 0; return; }
+    extern __shared__ __align__(16) char smem[];
+    EigSmem S(smem, n);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) S.A[e] = P.H[(e / n) * m + (e % n)];
+    __syncthreads();
+    eig_block(S.A, S.Q, n, n, nsel, lam, Yc, Zc, nsel, work, work + (size_t)n * nsel, S.v, S.sh, S.ord);
+    for (int e = threadIdx.x; e < n * nsel; e += blockDim.x) {
+        const int row = e / nsel;
+        Yc[e] = P.vscale[row] * Yc[e];
+        Zc[e] = P.wscale[row] * Zc[e];
+    }
+    if (threadIdx.x == 0) *nout = nsel;
+}
+
+// LU with partial pivoting, one CTA.
+__global__ void lu_factor_kernel(int n, double2* A, int lda, int* piv, int* info) {
+    __shared__ int s_p;
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            int p = k; double best = -1.0;
+            for (int i = k; i < n; ++i) { double v = cabs_(A[i * lda + k]); if (v > best) { best = v; p = i; } }
+            s_p = p; piv[k] = p;
+            if (best == 0.0) s_bad = 1;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k)
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                double2 t = A[k * lda + j]; A[k * lda + j] = A[p * lda + j]; A[p * lda + j] = t;
+            }
+        __syncthreads();
+        const double2 d = A[k * lda + k];
+        if (cabs2(d) > 0.0)
+            for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * lda + k] = cdiv(A[i * lda + k], d);
+        __syncthreads();
+        for (int e = threadIdx.x; e < (n - k - 1) * (n - k - 1); e += blockDim.x) {
+            const int i = k + 1 + e / (n - k - 1), j = k + 1 + e % (n - k - 1);
+            A[i * lda + j] = A[i * lda + j] - A[i * lda + k] * A[k * lda + j];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && info) *info = s_bad;
+}
+
+// Solve with the LU factors; one thread per right-hand-side column.
+__global__ void lu_solve_kernel(int n, const double2* LU, int lda, const int* piv, int trans, int nrhs,
+                                double2* B, int ldb) {
+    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
+        if (!trans) {
+            for (int k = 0; k < n; ++k) {   // P
+                int p = piv[k];
+                if (p != k) { double2 t = B[k * ldb + c]; B[k * ldb + c] = B[p * ldb + c]; B[p * ldb + c] = t; }
+            }
+            for (int i = 0; i < n; ++i) {   // L y = b
+                double2 acc = B[i * ldb + c];
+                for (int j = 0; j < i; ++j) acc = acc - LU[i * lda + j] * B[j * ldb + c];
+                B[i * ldb + c] = acc;
+            }
+            for (int i = n - 1; i >= 0; --i) {   // U x = y
+                double2 acc = B[i * ldb + c];
+                for (int j = i + 1; j < n; ++j) acc = acc - LU[i * lda + j] * B[j * ldb + c];
+                B[i * ldb + c] = cdiv(acc, LU[i * lda + i]);
+            }
+        } else {
+            // A^H x = b with P A = L U:  A^H = U^H L^H P  ->  U^H y = b, L^H w = y, x = P^T w
+            for (int i = 0; i < n; ++i) {
+                double2 acc = B[i * ldb + c];
+                for (int j = 0; j < i; ++j) acc = acc - conj_(LU[j * lda + i]) * B[j * ldb + c];
+                B[i * ldb + c] = cdiv(acc, conj_(LU[i * lda + i]));
+            }
+            for (int i = n - 1; i >= 0; --i) {
+                double2 acc = B[i * ldb + c];
+                for (int j = i + 1; j < n; ++j) acc = acc - conj_(LU[j * lda + i]) * B[j * ldb + c];
+                B[i * ldb + c] = acc;
+            }
+            for (int k = n - 1; k >= 0; --k) {
+                int p = piv[k];
+                if (p != k) { double2 t = B[k * ldb + c]; B[k * ldb + c] = B[p * ldb + c]; B[p * ldb + c] = t; }
+            }
+        }
+    }
+}
+
+__global__ void small_gemm_kernel(int n, int k, int m, const double2* A, int lda, int transA,
+                                  const double2* B, int ldb, double2* C, int ldc) {
+    for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < n * m; e += blockDim.x * gridDim.x) {
+        const int i = e / m, j = e % m;
+        double2 acc = czero();
+        for (int l = 0; l < k; ++l) {
+            double2 a = transA ? conj_(A[l * lda + i]) : A[i * lda + l];
+            acc = acc + a * B[l * ldb + j];
+        }
+        C[i * ldc + j] = acc;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+static cudaError_t set_smem(const void* fn, size_t bytes) {
+    if (bytes > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+cudaError_t prepare_eig_kernels() {
+    cudaError_t e;
+    if ((e = set_smem((const void*)small_eig_kernel, EigSmem::bytes(MAX_SMALL))) != cudaSuccess) return e;
+    if ((e = set_smem((const void*)restart_single_kernel, EigSmem::bytes(MAX_M))) != cudaSuccess) return e;
+    if ((e = set_smem((const void*)restart_slots_kernel, EigSmem::bytes(MAX_M))) != cudaSuccess) return e;
+    return set_smem((const void*)final_ritz_kernel, EigSmem::bytes(MAX_M));
+}
+
+size_t eig_work_elems() {
+    size_t a = RestartWork::elems(MAX_M, MAX_M / 2);
+    size_t b = (size_t)2 * MAX_SMALL * MAX_SMALL + 16;
+    return a > b ? a : b;
+}
+
+cudaError_t launch_small_eig(int n, const double2* A, int lda, int nsel, double2* lam, double2* Y, double2* Z,
+                             int ldyz, int* info, double2* w, cudaStream_t st) {
+    if (n < 1 || n > MAX_SMALL) return cudaErrorInvalidValue;
+    size_t sm = EigSmem::bytes(n);
+    cudaError_t e = set_smem((const void*)small_eig_kernel, sm);
+    if (e != cudaSuccess) return e;
+    small_eig_kernel<<<1, ET, sm, st>>>(n, A, lda, nsel, lam, Y, Z, ldyz, w, info);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restart_coeffs_single(int m, int nev, const double2* H, int* r, double2* Yc, double2* Zc,
+                                         double2* lam, int* info, double2* w, cudaStream_t st) {
+    if (m < 3 || m > MAX_M || 2 * nev >= m || nev < 1) return cudaErrorInvalidValue;
+    size_t sm = EigSmem::bytes(m);
+    cudaError_t e = set_smem((const void*)restart_single_kernel, sm);
+    if (e != cudaSuccess) return e;
+    restart_single_kernel<<<1, ET, sm, st>>>(m, nev, H, r, Yc, Zc, lam, w, info);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restart_coeffs(SlotState* states, const SlotPtrs* ptrs, int nslots, double2* w,
+                                  cudaStream_t st) {
+    // Per-slot work stride: capacity for the largest window.
+    // (dynamic shared memory opt-in done once by prepare_eig_kernels: this launcher runs under graph capture)
+    const size_t stride = eig_work_elems();
+    size_t sm = EigSmem::bytes(MAX_M);
+    restart_slots_kernel<<<nslots, ET, sm, st>>>(states, ptrs, w, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_ritz(SlotState* states, const SlotPtrs* ptrs, int slot, double2* Yc, double2* Zc,
+                              double2* lam, int* nout, double2* w, cudaStream_t st) {
+    size_t sm = EigSmem::bytes(MAX_M);
+    final_ritz_kernel<<<1, ET, sm, st>>>(states, ptrs, slot, Yc, Zc, lam, nout, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lu_factor(int n, double2* A, int lda, int* piv, int* info, cudaStream_t st) {
+    lu_factor_kernel<<<1, 256, 0, st>>>(n, A, lda, piv, info);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lu_solve(int n, const double2* LU, int lda, const int* piv, int trans, int nrhs, double2* B,
+                            int ldb, cudaStream_t st) {
+    lu_solve_kernel<<<1, 128, 0, st>>>(n, LU, lda, piv, trans, nrhs, B, ldb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_small_gemm(int n, int k, int m, const double2* A, int lda, int transA, const double2* B,
+                              int ldb, double2* C, int ldc, cudaStream_t st) {
+    int blocks = (n * m + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    small_gemm_kernel<<<blocks, 256, 0, st>>>(n, k, m, A, lda, transA, B, ldb, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace lqcd

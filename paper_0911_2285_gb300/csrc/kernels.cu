@@ -1,0 +1,790 @@
+// Lattice-sized kernels: the Wilson operator applications, the BiCG iteration
+// (Algorithm eigBiCG, steps 1-3 of the paper, Sec. 2), the window product of
+// the BiCG-eigen restart with its coupling row/column, and the tall-skinny
+// products of the oblique deflation (Algorithm Incremental eigBiCG).
+//
+// All reductions are two-level and deterministic: each block writes its
+// partial sums to a fixed slot, and the last block to finish adds them in
+// block order (same result alone or inside a batch).
+#include "dslash.cuh"
+#include "kernels.cuh"
+
+namespace lqcd {
+namespace {
+
+constexpr int DS_THREADS = 128;   // operator kernels
+constexpr int BL_THREADS = 256;   // vector kernels
+constexpr double BREAK_TOL = 1e-14;
+
+inline int div_up(size_t a, size_t b) { return (int)((a + b - 1) / b); }
+
+int blas_blocks(size_t units) {
+    int nb = div_up(units, BL_THREADS);
+    if (nb > 1216) nb = 1216;   // 8 blocks of 256 per SM on 152 SMs
+    if (nb < 1) nb = 1;
+    return nb;
+}
+int ds_blocks(int V) {
+    int nb = div_up((size_t)V, DS_THREADS);
+    if (nb > PARTIAL_STRIDE / 2) nb = PARTIAL_STRIDE / 2;
+    return nb;
+}
+
+__device__ __forceinline__ double2* part(const SlotPtrs& P, int kind) { return P.partials + (size_t)kind * PARTIAL_STRIDE; }
+
+// Sum NV complex values per block into part[kind][block*NV + i]; in the last
+// block returns true with tot[] = sum over blocks (thread 0 only).
+template <int NV>
+__device__ bool reduce_slot(const SlotPtrs& P, int kind, double2 (&v)[NV], double2 (&tot)[NV], unsigned nblocks,
+                            unsigned bid) {
+    __shared__ double2 sm[(BL_THREADS / 32) * NV];   // blockDim.x <= BL_THREADS
+    block_sum<NV>(v, sm);
+    double2* pp = part(P, kind);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) pp[(size_t)bid * NV + i] = v[i];
+    }
+    bool last = last_block(P.counters + kind, nblocks);
+    if (last) {
+        // the last block adds the partials in block order (deterministic)
+        double2 acc[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] = make_double2(0.0, 0.0);
+        for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) acc[i] = acc[i] + __ldcg(pp + (size_t)b * NV + i);
+        // fixed-order tree over threads
+        block_sum<NV>(acc, sm);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) tot[i] = acc[i];
+    }
+    return last;
+}
+
+// ------------------------------------------------------------------- apply
+template <typename S, bool RES>
+__global__ void __launch_bounds__(DS_THREADS) apply_kernel(Geom g, const void* links, double kappa,
+                                                           const ApplyJob* jobs) {
+    using C = cplx<S>;
+    const ApplyJob jb = jobs[blockIdx.y];
+    typename LinkSel<S>::type U{reinterpret_cast<decltype(U.u)>(links), g.V};
+    FieldIn<S> in{jb.in, g.V};
+    const S k = (S)kappa;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        C acc[12], self[12];
+        if (jb.dagger) hop_site<true, S>(g, U, in, s, acc);
+        else hop_site<false, S>(g, U, in, s, acc);
+        in.load(s, self);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = self[c] - k * acc[c];
+        if (RES) {
+            double2 b[12];
+            Field<double>::load(jb.aux, g.V, s, b);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[c] = cvt<S>(b[c] - to_d(acc[c]));
+        }
+        Field<S>::store(jb.out, g.V, s, acc);
+    }
+}
+
+// -------------------------------------------------------------- pack/unpack
+// Host layout AoS [site][12] complex128 <-> device chunk layout.
+template <typename S>
+__global__ void pack_kernel(const double2* aos, void* dev, int V, int k) {
+    const size_t total = (size_t)V * 12 * k;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t f = i / ((size_t)V * 12);
+        const size_t r = i % ((size_t)V * 12);
+        const int s = (int)(r / 12), c = (int)(r % 12);
+        const size_t e = f * (size_t)V * 12 + ((size_t)(c >> 1) * V + s) * 2 + (c & 1);
+        st_elem<S>(dev, e, cvt<S>(aos[i]));
+    }
+}
+template <typename S>
+__global__ void unpack_kernel(const void* dev, double2* aos, int V, int k) {
+    const size_t total = (size_t)V * 12 * k;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t f = i / ((size_t)V * 12);
+        const size_t r = i % ((size_t)V * 12);
+        const int s = (int)(r / 12), c = (int)(r % 12);
+        const size_t e = f * (size_t)V * 12 + ((size_t)(c >> 1) * V + s) * 2 + (c & 1);
+        aos[i] = to_d(ld_elem<S>(dev, e));
+    }
+}
+template <typename SI, typename SO>
+__global__ void convert_kernel(const void* src, void* dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        st_elem<SO>(dst, i, cvt<SO>(to_d(ld_elem<SI>(src, i))));
+}
+
+// ------------------------------------------------------------- multidot
+// C[i][j] = sum_e conj(X_i(e)) Y_j(e) for i in [i0, i0+TI), j < b <= BMAX.
+constexpr int MD_TI = 4, MD_BMAX = 8;
+template <typename SX, typename SY, typename T>
+__global__ void __launch_bounds__(BL_THREADS) multidot_kernel(int a, const void* X, int b, const void* Y, size_t N,
+                                                              double2* scratch) {
+    using C = cplx<T>;
+    const int i0 = blockIdx.y * MD_TI;
+    C acc[MD_TI][MD_BMAX];
+#pragma unroll
+    for (int i = 0; i < MD_TI; ++i)
+#pragma unroll
+        for (int j = 0; j < MD_BMAX; ++j) acc[i][j] = mk<T>(T(0), T(0));
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+        C y[MD_BMAX];
+#pragma unroll
+        for (int j = 0; j < MD_BMAX; ++j)
+            if (j < b) {
+                auto v = ld_elem<SY>(reinterpret_cast<const char*>(Y) + (size_t)j * N * sizeof(cplx<SY>), e);
+                y[j] = mk<T>((T)v.x, (T)v.y);
+            }
+#pragma unroll
+        for (int i = 0; i < MD_TI; ++i)
+            if (i0 + i < a) {
+                auto v = ld_elem<SX>(reinterpret_cast<const char*>(X) + (size_t)(i0 + i) * N * sizeof(cplx<SX>), e);
+                C x = mk<T>((T)v.x, (T)v.y);
+#pragma unroll
+                for (int j = 0; j < MD_BMAX; ++j)
+                    if (j < b) acc[i][j] = acc[i][j] + cdot(x, y[j]);
+            }
+    }
+    double2 v[MD_TI * MD_BMAX];
+#pragma unroll
+    for (int i = 0; i < MD_TI; ++i)
+#pragma unroll
+        for (int j = 0; j < MD_BMAX; ++j) v[i * MD_BMAX + j] = to_d(acc[i][j]);
+    __shared__ double2 sm[(BL_THREADS / 32) * MD_TI * MD_BMAX];
+    block_sum<MD_TI * MD_BMAX>(v, sm);
+    if (threadIdx.x == 0) {
+        double2* out = scratch + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (MD_TI * MD_BMAX);
+#pragma unroll
+        for (int q = 0; q < MD_TI * MD_BMAX; ++q) out[q] = v[q];
+    }
+}
+__global__ void multidot_reduce_kernel(int a, int b, int nbx, const double2* scratch, double2* Cm, int ldc,
+                                       int conj_store) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;   // (i, j) pair
+    if (q >= a * b) return;
+    const int i = q / b, j = q % b;
+    const int by = i / MD_TI, ii = i % MD_TI;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int bx = 0; bx < nbx; ++bx) acc = acc + scratch[((size_t)by * nbx + bx) * (MD_TI * MD_BMAX) + ii * MD_BMAX + j];
+    if (conj_store) Cm[(size_t)j * ldc + i] = conj_(acc);
+    else Cm[(size_t)i * ldc + j] = acc;
+}
+
+// ------------------------------------------------------------- vupdate
+// mode 0: Y_j += sum_i X_i D[i][j];  mode 1: Y_j = sum_i X_i D[i][j]  (j < b <= MD_BMAX).
+template <typename SX, typename SY, typename T>
+__global__ void __launch_bounds__(BL_THREADS) vupdate_kernel(int a, const void* X, const double2* D, int ldd, int b,
+                                                             void* Y, int overwrite, size_t N) {
+    using C = cplx<T>;
+    __shared__ C Ds[MAX_SMALL * MD_BMAX];
+    for (int q = threadIdx.x; q < a * b; q += blockDim.x) {
+        const int i = q / b, j = q % b;
+        double2 d = D[(size_t)i * ldd + j];
+        Ds[i * MD_BMAX + j] = mk<T>((T)d.x, (T)d.y);
+    }
+    __syncthreads();
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+        C acc[MD_BMAX];
+#pragma unroll
+        for (int j = 0; j < MD_BMAX; ++j) acc[j] = mk<T>(T(0), T(0));
+        for (int i = 0; i < a; ++i) {
+            auto v = ld_elem<SX>(reinterpret_cast<const char*>(X) + (size_t)i * N * sizeof(cplx<SX>), e);
+            C x = mk<T>((T)v.x, (T)v.y);
+#pragma unroll
+            for (int j = 0; j < MD_BMAX; ++j)
+                if (j < b) acc[j] = acc[j] + x * Ds[i * MD_BMAX + j];
+        }
+#pragma unroll
+        for (int j = 0; j < MD_BMAX; ++j)
+            if (j < b) {
+                char* yj = reinterpret_cast<char*>(Y) + (size_t)j * N * sizeof(cplx<SY>);
+                double2 upd = to_d(acc[j]);
+                if (!overwrite) upd = upd + to_d(ld_elem<SY>(yj, e));   // add in the target precision
+                st_elem<SY>(yj, e, cvt<SY>(upd));
+            }
+    }
+}
+
+// Y_j *= s_j (per-field scale), j < b.
+template <typename S>
+__global__ void scale_fields_kernel(int b, void* Y, const double2* sc, size_t N) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N * b; q += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(q / N);
+        const double2 s = sc[j];
+        st_elem<S>(Y, q, cvt<S>(s * to_d(ld_elem<S>(Y, q))));
+    }
+}
+
+// ------------------------------------------------------------ BiCG kernels
+// Vector units: two complex numbers (one float4 in FP32, two double2 in FP64).
+template <typename S> struct Unit;
+template <> struct Unit<float> {
+    float2 a, b;
+    __device__ __forceinline__ static Unit load(const void* p, size_t u) {
+        float4 t = reinterpret_cast<const float4*>(p)[u];
+        return Unit{make_float2(t.x, t.y), make_float2(t.z, t.w)};
+    }
+    __device__ __forceinline__ void store(void* p, size_t u) const {
+        reinterpret_cast<float4*>(p)[u] = make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+template <> struct Unit<double> {
+    double2 a, b;
+    __device__ __forceinline__ static Unit load(const void* p, size_t u) {
+        const double2* d = reinterpret_cast<const double2*>(p);
+        return Unit{d[2 * u], d[2 * u + 1]};
+    }
+    __device__ __forceinline__ void store(void* p, size_t u) const {
+        double2* d = reinterpret_cast<double2*>(p);
+        d[2 * u] = a; d[2 * u + 1] = b;
+    }
+};
+
+// Start: r0 = b - A x_hi (already in r_true, FP64), rhat0 = r0, p = r, phat = rhat,
+// x_lo = 0; rho_0 = (rhat_0, r_0), ||r_0||, ||b||  (Algorithm eigBiCG, steps 1-2).
+template <typename S>
+__global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (st.status != ST_RUNNING) return;
+    using C = cplx<S>;
+    double2 v[2] = {make_double2(0, 0), make_double2(0, 0)};   // rho, (|r|^2, |b|^2)
+    const size_t units = N / 2;
+    Unit<S> zero{mk<S>(0, 0), mk<S>(0, 0)};
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+        Unit<double> rt = Unit<double>::load(P.r_true, u);
+        Unit<double> bb = Unit<double>::load(P.b, u);
+        Unit<S> r{cvt<S>(rt.a), cvt<S>(rt.b)};
+        r.store(P.V, u);
+        r.store(P.W, u);
+        r.store(P.p, u);
+        r.store(P.phat, u);
+        zero.store(P.x_lo, u);
+        double2 ra = to_d(r.a), rb = to_d(r.b);
+        v[0] = v[0] + cdot(ra, ra) + cdot(rb, rb);
+        v[1].x += cabs2(ra) + cabs2(rb);
+        v[1].y += cabs2(bb.a) + cabs2(bb.b);
+    }
+    double2 tot[2];
+    if (reduce_slot<2>(P, CNT_START, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+        st.rho = tot[0];
+        st.rnorm = sqrt(tot[1].x);
+        st.bnorm = sqrt(tot[1].y);
+        st.rhat_norm = st.rnorm;
+        st.rmax = st.rnorm;
+        st.true_rnorm = st.rnorm;
+        st.iter = 0; st.vs = 0; st.need_ru = 0; st.ru_count = 0; st.restarts = 0; st.restart_r = 0;
+        st.matvecs = 1; st.live = 1;
+        st.alpha_prev = make_double2(0, 0); st.beta_prev = make_double2(0, 0);
+        if (st.rnorm <= st.tol * st.bnorm) { st.status = ST_CONVERGED; st.live = 0; }
+    }
+    (void)sizeof(C);
+}
+
+// Operator pair of one iteration: A p -> Ap[par], A^+ phat -> Ahp[par];
+// sigma = (phat, A p) and alpha = rho / sigma in the last block.
+template <typename S>
+__global__ void __launch_bounds__(DS_THREADS) matvec_kernel(Geom g, const void* links, double kappa,
+                                                            SlotState* states, const SlotPtrs* ptrs) {
+    const int slot = blockIdx.y >> 1, which = blockIdx.y & 1;
+    SlotState& st = states[slot];
+    const SlotPtrs& P = ptrs[slot];
+    if (st.status != ST_RUNNING) return;
+    using C = cplx<S>;
+    const int par = st.iter & 1;
+    typename LinkSel<S>::type U{reinterpret_cast<decltype(U.u)>(links), g.V};
+    FieldIn<S> in{which ? P.phat : P.p, g.V};
+    void* out = which ? P.Ahp[par] : P.Ap[par];
+    const S k = (S)kappa;
+    double2 v[2] = {make_double2(0, 0), make_double2(0, 0)};   // sigma, (|phat|^2, |Ap|^2)
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        C acc[12], self[12];
+        if (which) hop_site<true, S>(g, U, in, s, acc);
+        else hop_site<false, S>(g, U, in, s, acc);
+        in.load(s, self);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = self[c] - k * acc[c];
+        Field<S>::store(out, g.V, s, acc);
+        if (!which) {
+            C ph[12];
+            Field<S>::load(P.phat, g.V, s, ph);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                double2 a = to_d(ph[c]), b = to_d(acc[c]);
+                v[0] = v[0] + cdot(a, b);
+                v[1].x += cabs2(a);
+                v[1].y += cabs2(b);
+            }
+        }
+    }
+    if (which) return;
+    double2 tot[2];
+    if (reduce_slot<2>(P, CNT_MATVEC, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+        st.sigma = tot[0];
+        st.phat_norm = sqrt(tot[1].x);
+        st.ap_norm = sqrt(tot[1].y);
+        st.matvecs += 2;
+        if (!(cabs_(st.sigma) >= BREAK_TOL * st.phat_norm * st.ap_norm) || cabs2(st.sigma) == 0.0) {
+            st.status = ST_BREAKDOWN;
+        } else {
+            st.alpha = cdiv(st.rho, st.sigma);
+        }
+    }
+}
+
+// x_lo += alpha p; r_j = r_{j-1} - alpha A p; rhat_j = rhat_{j-1} - conj(alpha) A^+ phat;
+// rho_j, ||r_j||, ||rhat_j||; flags for the FP64 residual check.
+template <typename S>
+__global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (st.status != ST_RUNNING) return;
+    using C = cplx<S>;
+    const int par = st.iter & 1;
+    const C al = cvt<S>(st.alpha), alc = conj_(al);
+    const void* rin = slot_field<S>(P.V, cur_slot(st), N);
+    void* rout = slot_field<S>(P.V, next_slot(st), N);
+    const void* hin = slot_field<S>(P.W, cur_slot(st), N);
+    void* hout = slot_field<S>(P.W, next_slot(st), N);
+    const void* ap = P.Ap[par];
+    const void* ahp = P.Ahp[par];
+    double2 v[2] = {make_double2(0, 0), make_double2(0, 0)};
+    const size_t units = N / 2;
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+        Unit<S> x = Unit<S>::load(P.x_lo, u), p = Unit<S>::load(P.p, u);
+        Unit<S> r = Unit<S>::load(rin, u), a = Unit<S>::load(ap, u);
+        Unit<S> h = Unit<S>::load(hin, u), ah = Unit<S>::load(ahp, u);
+        x.a = x.a + al * p.a; x.b = x.b + al * p.b;
+        r.a = r.a - al * a.a; r.b = r.b - al * a.b;
+        h.a = h.a - alc * ah.a; h.b = h.b - alc * ah.b;
+        x.store(P.x_lo, u);
+        r.store(rout, u);
+        h.store(hout, u);
+        double2 ra = to_d(r.a), rb = to_d(r.b), ha = to_d(h.a), hb = to_d(h.b);
+        v[0] = v[0] + cdot(ha, ra) + cdot(hb, rb);
+        v[1].x += cabs2(ra) + cabs2(rb);
+        v[1].y += cabs2(ha) + cabs2(hb);
+    }
+    double2 tot[2];
+    if (reduce_slot<2>(P, CNT_UPDATE, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+        st.rho_new = tot[0];
+        st.rnorm_new = sqrt(tot[1].x);
+        st.rhat_norm = sqrt(tot[1].y);
+        if (!isfinite(st.rnorm_new) || !isfinite(st.rho_new.x) || !isfinite(st.rho_new.y)) {
+            st.status = ST_BREAKDOWN;
+        } else {
+            if (st.rnorm_new <= st.tol * st.bnorm) st.need_ru = 1;
+            if (st.delta > 0.0 && st.rnorm_new < st.delta * st.rmax) st.need_ru = 1;
+            if (st.rnorm_new > st.rmax) st.rmax = st.rnorm_new;
+        }
+    }
+}
+
+// FP64 true residual r = b - A (x_hi + x_lo) for slots that asked for it.
+// check_only = 0: inside the iteration (converged if ||r|| <= tol ||b||);
+// check_only = 1: final report for every slot that was started.
+template <typename S>
+__global__ void __launch_bounds__(DS_THREADS) true_resid_kernel(Geom g, const void* links64, double kappa,
+                                                                SlotState* states, const SlotPtrs* ptrs,
+                                                                int check_only) {
+    SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (check_only) {
+        if (st.status == ST_IDLE) return;
+    } else if (st.status != ST_RUNNING || !st.need_ru) {
+        return;
+    }
+    LinksD U{reinterpret_cast<const double2*>(links64), g.V};
+    SumIn<S> in{P.x_hi, P.x_lo, g.V};
+    double2 v[1] = {make_double2(0, 0)};
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        double2 acc[12], self[12], b[12];
+        hop_site<false, double>(g, U, in, s, acc);
+        in.load(s, self);
+        Field<double>::load(P.b, g.V, s, b);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            acc[c] = b[c] - (self[c] - kappa * acc[c]);
+            v[0].x += cabs2(acc[c]);
+        }
+        Field<double>::store(P.r_true, g.V, s, acc);
+    }
+    double2 tot[1];
+    if (reduce_slot<1>(P, CNT_RU, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+        st.true_rnorm = sqrt(tot[0].x);
+        st.matvecs += 1;
+        if (!check_only && st.true_rnorm <= st.tol * st.bnorm) st.status = ST_CONVERGED;
+    }
+}
+
+// Reliable update: x_hi += x_lo, x_lo = 0; unless converged, the recursive
+// residual r_j is replaced by the true one and rho_j recomputed.
+template <typename S>
+__global__ void __launch_bounds__(BL_THREADS) replace_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (!st.live || !st.need_ru || (st.status != ST_RUNNING && st.status != ST_CONVERGED)) return;
+    const bool run = st.status == ST_RUNNING;
+    void* rcur = slot_field<S>(P.V, next_slot(st), N);
+    const void* hcur = slot_field<S>(P.W, next_slot(st), N);
+    double2 v[1] = {make_double2(0, 0)};
+    const size_t units = N / 2;
+    Unit<S> zero{mk<S>(0, 0), mk<S>(0, 0)};
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+        Unit<double> xh = Unit<double>::load(P.x_hi, u);
+        Unit<S> xl = Unit<S>::load(P.x_lo, u);
+        xh.a = xh.a + to_d(xl.a); xh.b = xh.b + to_d(xl.b);
+        xh.store(P.x_hi, u);
+        zero.store(P.x_lo, u);
+        if (run) {
+            Unit<double> rt = Unit<double>::load(P.r_true, u);
+            Unit<S> r{cvt<S>(rt.a), cvt<S>(rt.b)};
+            r.store(rcur, u);
+            Unit<S> h = Unit<S>::load(hcur, u);
+            v[0] = v[0] + cdot(to_d(h.a), to_d(r.a)) + cdot(to_d(h.b), to_d(r.b));
+        }
+    }
+    double2 tot[1];
+    if (reduce_slot<1>(P, CNT_REPLACE, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+        if (run) {
+            st.rho_new = tot[0];
+            st.rnorm_new = st.true_rnorm;
+            st.rmax = st.true_rnorm;
+        }
+        st.need_ru = 0;
+        st.ru_count += 1;
+    }
+}
+
+// Scalar bookkeeping of one iteration (one thread per slot):
+// beta_{j-1} = rho_j / rho_{j-1}; window append v = r/||r||, w = (||r||/conj(rho)) rhat;
+// tridiagonal entries of H (Algorithm eigBiCG, step 3); iteration counters.
+__global__ void scalars_kernel(SlotState* states, const SlotPtrs* ptrs) {
+    if (threadIdx.x != 0) return;
+    SlotState& st = states[blockIdx.x];
+    const SlotPtrs& P = ptrs[blockIdx.x];
+    if (!st.live) return;
+    if (st.status == ST_BREAKDOWN) { st.live = 0; return; }
+    const double2 beta = cdiv(st.rho_new, st.rho);
+    if (st.m > 0) {
+        const int k = st.vs;   // 0-based index of the appended vector
+        const int m = st.m;
+        P.vscale[k] = 1.0 / st.rnorm;
+        P.wscale[k] = cdiv(make_double2(st.rnorm, 0.0), conj_(st.rho));
+        const double2 inv_a = cdiv(make_double2(1.0, 0.0), st.alpha);
+        double2 diag = inv_a;
+        if (st.iter > 0) diag = diag + cdiv(st.beta_prev, st.alpha_prev);
+        P.H[k * m + k] = diag;
+        if (k + 1 < m) {
+            P.H[k * m + k + 1] = -(st.rnorm / st.rnorm_new) * cdiv(beta, st.alpha);
+            P.H[(k + 1) * m + k] = -(st.rnorm_new / st.rnorm) * inv_a;
+        }
+        st.vs = k + 1;
+    }
+    st.beta = beta;
+    st.alpha_prev = st.alpha;
+    st.beta_prev = beta;
+    st.rho = st.rho_new;
+    st.rnorm = st.rnorm_new;
+    st.iter += 1;
+    if (st.status == ST_RUNNING) {
+        if (st.iter >= st.maxiter) st.status = ST_NOCONV;
+        else if (!(cabs_(st.rho) >= BREAK_TOL * st.rhat_norm * st.rnorm)) st.status = ST_BREAKDOWN;
+    }
+    if (st.status != ST_RUNNING) st.live = 0;
+}
+
+// p_j = r_j + beta p_{j-1}, phat_j = rhat_j + conj(beta) phat_{j-1}.
+template <typename S>
+__global__ void __launch_bounds__(BL_THREADS) direction_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    const SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (st.status != ST_RUNNING) return;
+    using C = cplx<S>;
+    const C be = cvt<S>(st.beta), bec = conj_(be);
+    const void* r = slot_field<S>(P.V, cur_slot(st), N);
+    const void* h = slot_field<S>(P.W, cur_slot(st), N);
+    const size_t units = N / 2;
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+        Unit<S> p = Unit<S>::load(P.p, u), ph = Unit<S>::load(P.phat, u);
+        Unit<S> rr = Unit<S>::load(r, u), hh = Unit<S>::load(h, u);
+        p.a = rr.a + be * p.a; p.b = rr.b + be * p.b;
+        ph.a = hh.a + bec * ph.a; ph.b = hh.b + bec * ph.b;
+        p.store(P.p, u);
+        ph.store(P.phat, u);
+    }
+}
+
+// Fold x_lo into x_hi at the end of a solve (x = 0 for a zero source).
+template <typename S>
+__global__ void fold_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    const SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (st.status == ST_IDLE) return;
+    const bool zero_src = st.bnorm == 0.0;
+    const size_t units = N / 2;
+    Unit<S> zero{mk<S>(0, 0), mk<S>(0, 0)};
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+        Unit<double> xh = Unit<double>::load(P.x_hi, u);
+        Unit<S> xl = Unit<S>::load(P.x_lo, u);
+        if (zero_src) { xh.a = make_double2(0, 0); xh.b = make_double2(0, 0); }
+        else { xh.a = xh.a + to_d(xl.a); xh.b = xh.b + to_d(xl.b); }
+        xh.store(P.x_hi, u);
+        zero.store(P.x_lo, u);
+    }
+}
+
+// -------------------------------------------------------- restart product
+// In-place window product of the BiCG-eigen restart (one job per slot and side):
+//   new slot k = sum_{i<m} scale_i coef[i][k] old slot i   (k < r)
+//   new slot r = old slot m                                  (r_{j-1}, appended next)
+// with the coupling dots of the new vectors:
+//   V side: H[r][k] = (||r_{j-1}|| / rho_{j-1}) (A^+ phat - conj(beta_{j-2}) s)^H v_k
+//   W side: H[k][r] = (1 / ||r_{j-1}||) w_k^H (A p - beta_{j-2} q)
+// where q, s are the products of the previous iteration (Algorithm eigBiCG).
+template <typename S, int RMAX>
+__global__ void __launch_bounds__(BL_THREADS) window_gemm_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+    SlotState& st = states[slot];
+    const SlotPtrs& P = ptrs[slot];
+    if (st.status != ST_RUNNING || st.restart_r == 0) return;
+    using C = cplx<S>;
+    const int m = st.m, r = st.restart_r, ldc = 2 * st.nev + 1;
+    const int par = st.iter & 1;
+    __shared__ C Cs[(MAX_M + 1) * RMAX];
+    const double2* coef = side ? P.coefZ : P.coefY;
+    for (int q = threadIdx.x; q < m * r; q += blockDim.x) {
+        const int i = q / r, k = q % r;
+        double2 sc = side ? P.wscale[i] : make_double2(P.vscale[i], 0.0);
+        Cs[i * RMAX + k] = cvt<S>(sc * coef[i * ldc + k]);
+    }
+    __syncthreads();
+    // coupling vector: V side c = A^+phat - conj(beta) s ; W side a = A p - beta q
+    const C bp = cvt<S>(side ? st.beta_prev : conj_(st.beta_prev));
+    const void* cur = side ? P.Ap[par] : P.Ahp[par];
+    const void* prv = side ? P.Ap[par ^ 1] : P.Ahp[par ^ 1];
+    void* base = side ? P.W : P.V;
+    C dot[RMAX];
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) dot[k] = mk<S>(S(0), S(0));
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+        C out[RMAX];
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) out[k] = mk<S>(S(0), S(0));
+        for (int i = 0; i < m; ++i) {
+            const C x = ld_elem<S>(slot_field<S>(base, i, N), e);
+#pragma unroll
+            for (int k = 0; k < RMAX; ++k)
+                if (k < r) out[k] = out[k] + x * Cs[i * RMAX + k];
+        }
+        const C last = ld_elem<S>(slot_field<S>(base, m, N), e);
+        const C cv = ld_elem<S>(cur, e) - bp * ld_elem<S>(prv, e);
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k)
+            if (k < r) {
+                st_elem<S>(slot_field<S>(base, k, N), e, out[k]);
+                dot[k] = dot[k] + (side ? cdot(out[k], cv) : cdot(cv, out[k]));
+            }
+        st_elem<S>(slot_field<S>(base, r, N), e, last);
+    }
+    double2 v[RMAX];
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) v[k] = to_d(dot[k]);
+    double2 tot[RMAX];
+    if (reduce_slot<RMAX>(P, side ? CNT_GEMM_W : CNT_GEMM_V, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+        if (side) {
+            const double f = 1.0 / st.rnorm;
+            for (int k = 0; k < r; ++k) P.H[k * m + r] = f * tot[k];
+        } else {
+            const double2 f = cdiv(make_double2(st.rnorm, 0.0), st.rho);
+            for (int k = 0; k < r; ++k) P.H[r * m + k] = f * tot[k];
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+static Geom geom_of(const Geom& g) { return g; }
+
+cudaError_t launch_apply(const Geom& g, const void* links, double kappa, int precision, const ApplyJob* d_jobs,
+                         int njobs, int residual, cudaStream_t st) {
+    dim3 grid(ds_blocks(g.V), njobs);
+    if (precision == 0) {
+        if (residual) apply_kernel<double, true><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs);
+        else apply_kernel<double, false><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs);
+    } else {
+        if (residual) return cudaErrorInvalidValue;
+        apply_kernel<float, false><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const double* aos, void* dev, int V, int k, int precision, cudaStream_t st) {
+    int nb = blas_blocks((size_t)V * 12 * k);
+    if (precision == 0) pack_kernel<double><<<nb, BL_THREADS, 0, st>>>(reinterpret_cast<const double2*>(aos), dev, V, k);
+    else pack_kernel<float><<<nb, BL_THREADS, 0, st>>>(reinterpret_cast<const double2*>(aos), dev, V, k);
+    return cudaGetLastError();
+}
+cudaError_t launch_unpack(const void* dev, double* aos, int V, int k, int precision, cudaStream_t st) {
+    int nb = blas_blocks((size_t)V * 12 * k);
+    if (precision == 0) unpack_kernel<double><<<nb, BL_THREADS, 0, st>>>(dev, reinterpret_cast<double2*>(aos), V, k);
+    else unpack_kernel<float><<<nb, BL_THREADS, 0, st>>>(dev, reinterpret_cast<double2*>(aos), V, k);
+    return cudaGetLastError();
+}
+cudaError_t launch_convert(const void* src, int sp, void* dst, int dp, size_t n, cudaStream_t st) {
+    int nb = blas_blocks(n);
+    if (sp == 0 && dp == 1) convert_kernel<double, float><<<nb, BL_THREADS, 0, st>>>(src, dst, n);
+    else if (sp == 1 && dp == 0) convert_kernel<float, double><<<nb, BL_THREADS, 0, st>>>(src, dst, n);
+    else if (sp == 0 && dp == 0) convert_kernel<double, double><<<nb, BL_THREADS, 0, st>>>(src, dst, n);
+    else convert_kernel<float, float><<<nb, BL_THREADS, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multidot(int a, const void* X, int xp, int b, const void* Y, int yp, size_t N, double2* Cm,
+                            int ldc, int conj_store, double2* scratch, size_t scratch_elems, cudaStream_t st) {
+    if (a <= 0 || b <= 0) return cudaSuccess;
+    for (int j0 = 0; j0 < b; j0 += MD_BMAX) {
+        const int bb = b - j0 < MD_BMAX ? b - j0 : MD_BMAX;
+        const int nby = div_up(a, MD_TI);
+        int nbx = blas_blocks(N) / 2;
+        if (nbx < 1) nbx = 1;
+        while ((size_t)nbx * nby * MD_TI * MD_BMAX > scratch_elems && nbx > 1) nbx /= 2;
+        if ((size_t)nbx * nby * MD_TI * MD_BMAX > scratch_elems) return cudaErrorInvalidValue;
+        const char* Yj = reinterpret_cast<const char*>(Y) + (size_t)j0 * N * (yp == 0 ? 16 : 8);
+        dim3 grid(nbx, nby);
+        if (xp == 1 && yp == 1) multidot_kernel<float, float, float><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
+        else if (xp == 1 && yp == 0) multidot_kernel<float, double, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
+        else if (xp == 0 && yp == 1) multidot_kernel<double, float, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
+        else multidot_kernel<double, double, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        double2* Cj = conj_store ? Cm + j0 * ldc : Cm + j0;
+        multidot_reduce_kernel<<<div_up((size_t)a * bb, 128), 128, 0, st>>>(a, bb, nbx, scratch, Cj, ldc, conj_store);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_vupdate(int a, const void* X, int xp, const double2* D, int ldd, int b, void* Y, int yp,
+                           int overwrite, size_t N, cudaStream_t st) {
+    if (a > MAX_SMALL) return cudaErrorInvalidValue;
+    for (int j0 = 0; j0 < b; j0 += MD_BMAX) {
+        const int bb = b - j0 < MD_BMAX ? b - j0 : MD_BMAX;
+        char* Yj = reinterpret_cast<char*>(Y) + (size_t)j0 * N * (yp == 0 ? 16 : 8);
+        const double2* Dj = D + j0;
+        int nb = blas_blocks(N);
+        if (xp == 1 && yp == 1) vupdate_kernel<float, float, float><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
+        else if (xp == 1 && yp == 0) vupdate_kernel<float, double, float><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
+        else if (xp == 0 && yp == 1) vupdate_kernel<double, float, double><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
+        else vupdate_kernel<double, double, double><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_scale_fields(int b, void* Y, int yp, const double2* sc, size_t N, cudaStream_t st) {
+    int nb = blas_blocks(N * b);
+    if (yp == 0) scale_fields_kernel<double><<<nb, BL_THREADS, 0, st>>>(b, Y, sc, N);
+    else scale_fields_kernel<float><<<nb, BL_THREADS, 0, st>>>(b, Y, sc, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_start(const Geom& g, const void* links64, double kappa, int prec, SlotState* states,
+                              const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s) {
+    (void)g; (void)links64; (void)kappa;
+    dim3 grid(blas_blocks(N / 2), nslots);
+    if (prec == 0) start_kernel<double><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    else start_kernel<float><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
+                               const SlotPtrs* ptrs, int nslots, cudaStream_t s) {
+    dim3 grid(ds_blocks(g.V), 2 * nslots);
+    if (prec == 0) matvec_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links, kappa, states, ptrs);
+    else matvec_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links, kappa, states, ptrs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_update(int prec, SlotState* states, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s) {
+    dim3 grid(blas_blocks(N / 2), nslots);
+    if (prec == 0) update_kernel<double><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    else update_kernel<float><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int prec, SlotState* states,
+                           const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s) {
+    dim3 grid(ds_blocks(g.V), nslots);
+    if (prec == 0) true_resid_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 0);
+    else true_resid_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 g2(blas_blocks(N / 2), nslots);
+    if (prec == 0) replace_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
+    else replace_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_scalars(SlotState* states, const SlotPtrs* ptrs, int nslots, cudaStream_t s) {
+    scalars_kernel<<<nslots, 32, 0, s>>>(states, ptrs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_direction(int prec, SlotState* states, const SlotPtrs* ptrs, int nslots, size_t N,
+                                  cudaStream_t s) {
+    dim3 grid(blas_blocks(N / 2), nslots);
+    if (prec == 0) direction_kernel<double><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    else direction_kernel<float><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa, int prec, SlotState* states,
+                               const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s) {
+    dim3 g2(blas_blocks(N / 2), nslots);
+    if (prec == 0) fold_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
+    else fold_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid(ds_blocks(g.V), nslots);
+    if (prec == 0) true_resid_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 1);
+    else true_resid_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 1);
+    return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t window_gemm_dispatch(int rmax_needed, SlotState* states, const SlotPtrs* ptrs, int nslots,
+                                        size_t N, cudaStream_t s) {
+    int nb = blas_blocks(N);
+    dim3 grid(nb, 2 * nslots);
+    if (rmax_needed <= 8) {
+        grid.x = nb < PARTIAL_STRIDE / 8 ? nb : PARTIAL_STRIDE / 8;
+        window_gemm_kernel<S, 8><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    } else if (rmax_needed <= 16) {
+        grid.x = nb < PARTIAL_STRIDE / 16 ? nb : PARTIAL_STRIDE / 16;
+        window_gemm_kernel<S, 16><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    } else if (rmax_needed <= 24) {
+        grid.x = nb < PARTIAL_STRIDE / 24 ? nb : PARTIAL_STRIDE / 24;
+        window_gemm_kernel<S, 24><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    } else if (rmax_needed <= 32) {
+        grid.x = nb < PARTIAL_STRIDE / 32 ? nb : PARTIAL_STRIDE / 32;
+        window_gemm_kernel<S, 32><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_gemm(int prec, int two_nev, SlotState* states, const SlotPtrs* ptrs, int nslots, size_t N,
+                               cudaStream_t s) {
+    if (prec == 0) return window_gemm_dispatch<double>(two_nev, states, ptrs, nslots, N, s);
+    return window_gemm_dispatch<float>(two_nev, states, ptrs, nslots, N, s);
+}
+
+}  // namespace lqcd

@@ -1,0 +1,86 @@
+// Host-side declarations of the kernel launchers (implemented in kernels.cu,
+// eig.cu). Every launcher enqueues on the given stream and returns the launch
+// error (cudaSuccess on success).
+#pragma once
+#include <cuda_runtime.h>
+#include "solver.cuh"
+
+namespace lqcd {
+
+constexpr int PARTIAL_STRIDE = 16384;  // double2 per counter kind per slot
+constexpr int MAX_SLOTS = 8;
+constexpr int MAX_M = 64;              // window size limit
+constexpr int MAX_SMALL = 80;          // largest dense eigenproblem / eigenspace
+
+struct ApplyJob {            // out = A in, A^+ in, or aux - A in
+    const void* in;
+    void* out;
+    const void* aux;         // FP64 b for the residual form
+    int dagger;
+};
+
+// precision: 0 = FP64 storage/arith (FP64 links), 1 = FP32 storage/arith (FP32 links)
+cudaError_t launch_apply(const Geom& g, const void* links, double kappa, int precision,
+                         const ApplyJob* d_jobs, int njobs, int residual, cudaStream_t st);
+
+// Host AoS complex128 [site][12] <-> device layout in storage precision.
+cudaError_t launch_pack(const double* aos, void* dev, int V, int k, int precision, cudaStream_t st);
+cudaError_t launch_unpack(const void* dev, double* aos, int V, int k, int precision, cudaStream_t st);
+// FP64 layout -> storage precision (element-wise), k fields.
+cudaError_t launch_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t n_elems, cudaStream_t st);
+
+// C[i*ldc + j] (+)= sum_e conj(X_i(e)) Y_j(e), i < a, j < b; X, Y fields of N complex.
+// conj_store: store conj(C) transposed, C[j*ldc + i] instead.
+cudaError_t launch_multidot(int a, const void* X, int xprec, int b, const void* Y, int yprec,
+                            size_t N, double2* C, int ldc, int conj_store, double2* scratch,
+                            size_t scratch_elems, cudaStream_t st);
+// overwrite = 0: Y_j += sum_i X_i D[i*ldd + j];  overwrite = 1: Y_j = sum_i X_i D[i*ldd + j].
+// The arithmetic is FP32 when X is FP32 (the sum is added to an FP64 Y in FP64).
+cudaError_t launch_vupdate(int a, const void* X, int xprec, const double2* D, int ldd, int b,
+                           void* Y, int yprec, int overwrite, size_t N, cudaStream_t st);
+// Y_j *= sc[j] for b fields (sc on the device).
+cudaError_t launch_scale_fields(int b, void* Y, int yprec, const double2* sc, size_t N, cudaStream_t st);
+
+// BiCG iteration kernels over nslots slots (see kernels.cu for the contract).
+cudaError_t launch_bicg_start(const Geom& g, const void* links, double kappa, int prec,
+                              SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec,
+                               SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s);
+cudaError_t launch_bicg_update(int prec, SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int prec,
+                           SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+cudaError_t launch_bicg_scalars(SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s);
+cudaError_t launch_bicg_direction(int prec, SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa, int prec,
+                               SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+
+// eigBiCG restart: coefficient kernel (one CTA per slot) and window product.
+// Work buffers: eig_work_elems() double2 per slot (restart) or per call (the others).
+size_t eig_work_elems();
+// Opt the eigen kernels into large dynamic shared memory (call once, outside graph capture).
+cudaError_t prepare_eig_kernels();
+cudaError_t launch_restart_coeffs(SlotState* st_, const SlotPtrs* ptrs, int nslots, double2* work, cudaStream_t s);
+cudaError_t launch_window_gemm(int prec, int two_nev, SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N,
+                               cudaStream_t s);
+
+// Small dense FP64 algebra on the device (one CTA).
+// eig of an n x n row-major matrix; Y, Z (n x nsel row-major columns) for the
+// nsel smallest-|lambda| eigenvalues; lam gets all n eigenvalues (sorted).
+cudaError_t launch_small_eig(int n, const double2* A, int lda, int nsel, double2* lam,
+                             double2* Y, double2* Z, int ldyz, int* info, double2* work, cudaStream_t st);
+cudaError_t launch_restart_coeffs_single(int m, int nev, const double2* H, int* r, double2* Yc,
+                                         double2* Zc, double2* lam, int* info, double2* work, cudaStream_t st);
+// LU with partial pivoting of n x n (row-major, in place), piv[n]; info != 0 if singular.
+cudaError_t launch_lu_factor(int n, double2* A, int lda, int* piv, int* info, cudaStream_t st);
+// Solve A X = B (trans = 0) or A^H X = B (trans = 1) with the LU factors; B is n x nrhs (ldb), in place.
+cudaError_t launch_lu_solve(int n, const double2* LU, int lda, const int* piv, int trans, int nrhs,
+                            double2* B, int ldb, cudaStream_t st);
+// Final Ritz pairs of one slot's window: eig(H^(vs)), nev smallest;
+// coefficients Y (vs x nev) and Z into Yc/Zc with the window scales folded in.
+cudaError_t launch_final_ritz(SlotState* st_, const SlotPtrs* ptrs, int slot, double2* Yc, double2* Zc,
+                              double2* lam, int* nout, double2* work, cudaStream_t st);
+// Small matrix helpers: C = A B (all row-major, n x k x m), one CTA.
+cudaError_t launch_small_gemm(int n, int k, int m, const double2* A, int lda, int transA,
+                              const double2* B, int ldb, double2* C, int ldc, cudaStream_t st);
+
+}  // namespace lqcd

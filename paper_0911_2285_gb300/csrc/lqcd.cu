@@ -1,0 +1,974 @@
+// Host side of the library: context, device memory, the solve driver and the
+// C ABI declared in include/lqcd.h.
+//
+// The driver follows Algorithm Incremental eigBiCG (paper Sec. 2): deflate the
+// initial guesses against the accumulated eigenspace, solve a batch of
+// right-hand sides with BiCG (eigBiCG while the eigenspace is still being
+// built), then bi-orthogonalize the new Ritz vectors against the eigenspace
+// and grow H = U_l^H A U_r. Every arithmetic step runs in the kernels of
+// kernels.cu / eig.cu; the host only launches, polls status words and copies
+// small matrices.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lqcd.h"
+#include "kernels.cuh"
+
+using namespace lqcd;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void set_error(const char* what, cudaError_t e) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    g_last_error = buf;
+}
+
+#define CK(call)                                                      \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) {                                      \
+            set_error(#call, e_);                                     \
+            return e_ == cudaErrorMemoryAllocation ? LQCD_ERR_OOM     \
+                                                   : LQCD_ERR_CUDA;   \
+        }                                                             \
+    } while (0)
+
+constexpr int CHECK_EVERY = 8;   // iterations per graph launch / status poll
+
+}  // namespace
+
+struct lqcd_ctx {
+    lqcd_params p{};
+    Geom g{};
+    int V = 0;
+    size_t N = 0;            // complex numbers per field
+    int kprec = 0;           // Krylov storage: 0 = FP64, 1 = FP32
+    size_t kbytes = 0;       // bytes per Krylov field
+    size_t dbytes = 0;       // bytes per FP64 field
+    int kmax = 1, m = 0, nev = 0, n_def_max = 0, nslot_win = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void*> allocs;
+
+    double2* links64 = nullptr;
+    float4* links32 = nullptr;
+
+    SlotState* d_state = nullptr;
+    SlotPtrs* d_ptrs = nullptr;
+    SlotState* h_state = nullptr;   // pinned mirror
+    std::vector<SlotPtrs> h_ptrs;
+
+    char* x_lo_all = nullptr;       // kmax Krylov fields
+    double2* x_hi_all = nullptr;    // kmax FP64 fields
+    double2* b_all = nullptr;
+    double2* rt_all = nullptr;
+    char* win_all = nullptr;        // kmax * 2 * (m+1) Krylov fields
+    char* vec_all = nullptr;        // kmax * 6 Krylov fields (p, phat, Ap[2], Ahp[2])
+    double2* small_all = nullptr;   // per-slot small matrices
+    size_t small_stride = 0;
+    double2* partials = nullptr;
+    unsigned* counters = nullptr;
+    double2* eigwork = nullptr;     // kmax * eig_work_elems()
+    double2* mdscratch = nullptr;
+    size_t mdscratch_elems = 0;
+    ApplyJob* d_jobs = nullptr;
+    double2* staging = nullptr;     // kmax FP64 fields (host AoS I/O)
+
+    // eigenspace
+    int n_def = 0;
+    int eig_rhs_done = 0;
+    char* Ur = nullptr;
+    char* Ul = nullptr;
+    double2* Hdef = nullptr;        // n_def_max^2, ld n_def_max
+    double2* Mdef = nullptr;
+    double2* Hlu = nullptr;
+    double2* Mlu = nullptr;
+    int* Hpiv = nullptr;
+    int* Mpiv = nullptr;
+    double2* dsmall = nullptr;      // scratch for small matrices (n_def_max * 16 * ...)
+    int* dinfo = nullptr;
+    double2* dconst = nullptr;      // constants
+
+    // CUDA graphs of CHECK_EVERY iterations, keyed by (nslots, windowed)
+    cudaGraphExec_t graphs[MAX_SLOTS + 1][2] = {};
+
+    // last eigBiCG window info (per slot): final Ritz values
+    std::vector<std::vector<double2>> last_ritz;
+    std::vector<int> last_vs, last_restarts;
+    int last_window_valid = 0;
+
+    template <typename T> cudaError_t alloc(T** p, size_t bytes) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+        if (e != cudaSuccess) return e;
+        allocs.push_back(q);
+        *p = reinterpret_cast<T*>(q);
+        return cudaSuccess;
+    }
+    void* krylov(char* base, size_t i) const { return base + i * kbytes; }
+};
+
+namespace {
+
+size_t small_stride_elems(int m, int nev) {
+    // H (m*m), wscale (m+1), coefY, coefZ ((m+1)*(2nev+1)), lam (2nev+2), vscale ((m+1) doubles -> as double2), ritz (nev)
+    return (size_t)m * m + (m + 1) + 2 * (size_t)(m + 1) * (2 * nev + 1) + (2 * nev + 2) + (m + 1) + nev + 16;
+}
+
+lqcd_status validate(const lqcd_params* p) {
+    if (!p) return LQCD_ERR_ARG;
+    for (int d = 0; d < 4; ++d)
+        if (p->dims[d] < 2 || p->dims[d] > 4096) return LQCD_ERR_ARG;
+    double V = (double)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3];
+    if (V * 12.0 > 2.0e9) return LQCD_ERR_ARG;
+    if (!(p->kappa >= 0.0) || !std::isfinite(p->kappa)) return LQCD_ERR_ARG;
+    if (p->nev < 1 || p->m <= 2 * p->nev || p->m > MAX_M || 2 * p->nev > 32) return LQCD_ERR_ARG;
+    if (!(p->tol > 0.0) || p->maxiter < 1) return LQCD_ERR_ARG;
+    if (p->precision != LQCD_FP64 && p->precision != LQCD_MIXED) return LQCD_ERR_ARG;
+    if (p->k_max < 0 || p->k_max > MAX_SLOTS) return LQCD_ERR_ARG;
+    if (p->n_def_max < 0 || p->n_def_max > MAX_SMALL) return LQCD_ERR_ARG;
+    if (p->n1 < 0 || p->deftol < 0.0 || p->delta < 0.0 || p->delta >= 1.0) return LQCD_ERR_ARG;
+    return LQCD_OK;
+}
+
+lqcd_status set_ptrs(lqcd_ctx* c) {
+    c->h_ptrs.resize(c->kmax);
+    for (int s = 0; s < c->kmax; ++s) {
+        SlotPtrs& P = c->h_ptrs[s];
+        P.x_lo = c->krylov(c->x_lo_all, s);
+        P.x_hi = c->x_hi_all + (size_t)s * c->N;
+        P.b = c->b_all + (size_t)s * c->N;
+        P.r_true = c->rt_all + (size_t)s * c->N;
+        const size_t wslots = (size_t)(c->m + 1);
+        P.V = c->krylov(c->win_all, (size_t)s * 2 * wslots);
+        P.W = c->krylov(c->win_all, (size_t)s * 2 * wslots + wslots);
+        char* vb = c->vec_all + (size_t)s * 6 * c->kbytes;
+        P.p = vb;
+        P.phat = vb + c->kbytes;
+        P.Ap[0] = vb + 2 * c->kbytes;
+        P.Ap[1] = vb + 3 * c->kbytes;
+        P.Ahp[0] = vb + 4 * c->kbytes;
+        P.Ahp[1] = vb + 5 * c->kbytes;
+        double2* sm = c->small_all + (size_t)s * c->small_stride;
+        const int m = c->m, nev = c->nev;
+        P.H = sm; sm += (size_t)m * m;
+        P.wscale = sm; sm += m + 1;
+        P.coefY = sm; sm += (size_t)(m + 1) * (2 * nev + 1);
+        P.coefZ = sm; sm += (size_t)(m + 1) * (2 * nev + 1);
+        P.lam = sm; sm += 2 * nev + 2;
+        P.vscale = reinterpret_cast<double*>(sm); sm += m + 1;
+        P.partials = c->partials + (size_t)s * CNT_COUNT * PARTIAL_STRIDE;
+        P.counters = c->counters + (size_t)s * CNT_COUNT;
+    }
+    CK(cudaMemcpy(c->d_ptrs, c->h_ptrs.data(), sizeof(SlotPtrs) * c->kmax, cudaMemcpyHostToDevice));
+    return LQCD_OK;
+}
+
+// Links: host [4][V][3][3] complex128 -> FP64 [mu][9][V] and FP32 two-row [mu][3][V].
+__global__ void links_kernel(const double2* host_layout, double2* l64, float4* l32, int V) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 4 * V; q += gridDim.x * blockDim.x) {
+        const int mu = q / V, s = q % V;
+        const double2* u = host_layout + (size_t)q * 9;
+        for (int e = 0; e < 9; ++e) l64[(size_t)(mu * 9 + e) * V + s] = u[e];
+        if (l32) {
+            l32[(size_t)(mu * 3 + 0) * V + s] = make_float4((float)u[0].x, (float)u[0].y, (float)u[1].x, (float)u[1].y);
+            l32[(size_t)(mu * 3 + 1) * V + s] = make_float4((float)u[2].x, (float)u[2].y, (float)u[3].x, (float)u[3].y);
+            l32[(size_t)(mu * 3 + 2) * V + s] = make_float4((float)u[4].x, (float)u[4].y, (float)u[5].x, (float)u[5].y);
+        }
+    }
+}
+
+__global__ void negate_kernel(double2* a, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = -a[i];
+}
+__global__ void copy_block_kernel(const double2* src, int lds, double2* dst, int ldd, int rows, int cols) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < rows * cols; q += gridDim.x * blockDim.x) {
+        const int i = q / cols, j = q % cols;
+        dst[(size_t)i * ldd + j] = src[(size_t)i * lds + j];
+    }
+}
+// sc[j] = 1/sqrt(diag(G)[j]) for G (n x n, ld), and nrm[j] = sqrt(diag)
+__global__ void inv_norm_kernel(const double2* G, int ld, int n, double2* sc, double* nrm) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double d = sqrt(fmax(G[(size_t)j * ld + j].x, 0.0));
+        nrm[j] = d;
+        sc[j] = make_double2(d > 0.0 ? 1.0 / d : 0.0, 0.0);
+    }
+}
+
+}  // namespace
+
+// ============================================================== lifecycle
+extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* params, const double* links,
+                                         void* cuda_stream) {
+    if (!out || !links) return LQCD_ERR_ARG;
+    *out = nullptr;
+    lqcd_status vs = validate(params);
+    if (vs != LQCD_OK) return vs;
+    lqcd_ctx* c = new lqcd_ctx();
+    c->p = *params;
+    if (c->p.k_max == 0) c->p.k_max = MAX_SLOTS;
+    if (c->p.delta == 0.0) c->p.delta = 0.1;
+    c->kmax = c->p.k_max;
+    c->m = c->p.m;
+    c->nev = c->p.nev;
+    c->n_def_max = c->p.n_def_max ? c->p.n_def_max : std::min(MAX_SMALL, std::max(c->p.n1, 1) * c->nev);
+    for (int d = 0; d < 4; ++d) c->g.L[d] = c->p.dims[d];
+    c->g.stride[0] = 1;
+    for (int d = 1; d < 4; ++d) c->g.stride[d] = c->g.stride[d - 1] * c->g.L[d - 1];
+    c->V = c->g.stride[3] * c->g.L[3];
+    c->g.V = c->V;
+    c->N = (size_t)12 * c->V;
+    c->kprec = c->p.precision == LQCD_MIXED ? 1 : 0;
+    c->kbytes = c->N * (c->kprec ? 8 : 16);
+    c->dbytes = c->N * 16;
+    c->small_stride = small_stride_elems(c->m, c->nev);
+    c->mdscratch_elems = (size_t)((MAX_SMALL + 3) / 4) * 1216 * 32;
+
+    // Memory plan (bytes) for the HBM budget check.
+    const size_t K = (size_t)c->kmax;
+    size_t plan = (size_t)c->V * 4 * 9 * 16 + (c->kprec ? (size_t)c->V * 4 * 3 * 16 : 0);
+    plan += K * c->kbytes * (1 + 2 * (c->m + 1) + 6) + K * c->dbytes * 4;
+    plan += 2 * (size_t)c->n_def_max * c->kbytes;
+    plan += K * eig_work_elems() * 16 + c->mdscratch_elems * 16 + K * CNT_COUNT * PARTIAL_STRIDE * 16;
+    if (c->p.hbm_budget_bytes && plan > c->p.hbm_budget_bytes) {
+        g_last_error = "memory plan exceeds hbm_budget_bytes";
+        delete c;
+        return LQCD_ERR_OOM;
+    }
+
+    auto fail = [&](lqcd_status s) { lqcd_destroy(c); return s; };
+    cudaError_t e;
+#define AL(ptr, bytes)                                                                   \
+    do {                                                                                 \
+        e = c->alloc(&(ptr), (bytes));                                                   \
+        if (e != cudaSuccess) { set_error("cudaMalloc " #ptr, e); return fail(e == cudaErrorMemoryAllocation ? LQCD_ERR_OOM : LQCD_ERR_CUDA); } \
+    } while (0)
+
+    if (cuda_stream) {
+        c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { set_error("cudaStreamCreate", e); delete c; return LQCD_ERR_CUDA; }
+        c->own_stream = true;
+    }
+    AL(c->links64, (size_t)c->V * 4 * 9 * 16);
+    if (c->kprec) AL(c->links32, (size_t)c->V * 4 * 3 * 16);
+    AL(c->d_state, sizeof(SlotState) * K);
+    AL(c->d_ptrs, sizeof(SlotPtrs) * K);
+    e = cudaMallocHost(&c->h_state, sizeof(SlotState) * K);
+    if (e != cudaSuccess) { set_error("cudaMallocHost", e); return fail(LQCD_ERR_OOM); }
+    AL(c->x_lo_all, K * c->kbytes);
+    AL(c->x_hi_all, K * c->dbytes);
+    AL(c->b_all, K * c->dbytes);
+    AL(c->rt_all, K * c->dbytes);
+    AL(c->win_all, K * 2 * (c->m + 1) * c->kbytes);
+    AL(c->vec_all, K * 6 * c->kbytes);
+    AL(c->small_all, K * c->small_stride * 16);
+    AL(c->partials, K * CNT_COUNT * PARTIAL_STRIDE * 16);
+    AL(c->counters, K * CNT_COUNT * sizeof(unsigned));
+    AL(c->eigwork, K * eig_work_elems() * 16);
+    AL(c->mdscratch, c->mdscratch_elems * 16);
+    AL(c->d_jobs, sizeof(ApplyJob) * 2 * K);
+    AL(c->staging, K * c->dbytes);
+    AL(c->Ur, (size_t)std::max(c->n_def_max, 1) * c->kbytes);
+    AL(c->Ul, (size_t)std::max(c->n_def_max, 1) * c->kbytes);
+    const size_t nd2 = (size_t)c->n_def_max * c->n_def_max + 16;
+    AL(c->Hdef, nd2 * 16);
+    AL(c->Mdef, nd2 * 16);
+    AL(c->Hlu, nd2 * 16);
+    AL(c->Mlu, nd2 * 16);
+    AL(c->Hpiv, (size_t)(c->n_def_max + 1) * sizeof(int));
+    AL(c->Mpiv, (size_t)(c->n_def_max + 1) * sizeof(int));
+    AL(c->dsmall, (size_t)(MAX_SMALL * MAX_SMALL * 6 + 4096) * 16);
+    AL(c->dinfo, 64 * sizeof(int));
+    AL(c->dconst, 64 * 16);
+#undef AL
+    if ((e = cudaMemset(c->counters, 0, K * CNT_COUNT * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemset(c->small_all, 0, K * c->small_stride * 16)) != cudaSuccess) {
+        set_error("cudaMemset", e);
+        return fail(LQCD_ERR_CUDA);
+    }
+    for (int s = 0; s < c->kmax; ++s) {
+        memset(&c->h_state[s], 0, sizeof(SlotState));
+        c->h_state[s].status = ST_IDLE;
+    }
+    if ((e = cudaMemcpy(c->d_state, c->h_state, sizeof(SlotState) * K, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        set_error("cudaMemcpy state", e);
+        return fail(LQCD_ERR_CUDA);
+    }
+    lqcd_status st = set_ptrs(c);
+    if (st != LQCD_OK) return fail(st);
+    // links: host -> staging (reuse rt_all as FP64 scratch of >= 4*V*9 complex? use a temp)
+    double2* tmp = nullptr;
+    if ((e = cudaMalloc(&tmp, (size_t)c->V * 4 * 9 * 16)) != cudaSuccess) { set_error("cudaMalloc links tmp", e); return fail(LQCD_ERR_OOM); }
+    e = cudaMemcpy(tmp, links, (size_t)c->V * 4 * 9 * 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        links_kernel<<<1216, 256, 0, c->stream>>>(tmp, c->links64, c->links32, c->V);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) { set_error("links upload", e); return fail(LQCD_ERR_CUDA); }
+    c->last_ritz.assign(c->kmax, {});
+    c->last_vs.assign(c->kmax, 0);
+    c->last_restarts.assign(c->kmax, 0);
+    if ((e = prepare_eig_kernels()) != cudaSuccess) { set_error("prepare_eig_kernels", e); return fail(LQCD_ERR_CUDA); }
+    *out = c;
+    return LQCD_OK;
+}
+
+extern "C" void lqcd_destroy(lqcd_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int i = 0; i <= MAX_SLOTS; ++i)
+        for (int j = 0; j < 2; ++j)
+            if (c->graphs[i][j]) cudaGraphExecDestroy(c->graphs[i][j]);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+extern "C" const char* lqcd_status_str(lqcd_status s) {
+    switch (s) {
+        case LQCD_OK: return "ok";
+        case LQCD_ERR_ARG: return "invalid argument";
+        case LQCD_ERR_OOM: return "out of device memory";
+        case LQCD_ERR_CUDA: return "CUDA error";
+        case LQCD_ERR_NOCONV: return "no convergence within maxiter";
+        case LQCD_ERR_BREAKDOWN: return "BiCG breakdown";
+        case LQCD_ERR_TIMEOUT: return "device wait timed out";
+        case LQCD_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* lqcd_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int lqcd_eigspace_size(const lqcd_ctx* c) { return c ? c->n_def : 0; }
+
+// ============================================================ field I/O
+namespace {
+
+// Copy k fields from user memory (host or device, AoS FP64) into device fields
+// of precision prec (0 FP64, 1 FP32), via the staging buffer for host input.
+lqcd_status upload(lqcd_ctx* c, const double* src, int k, void* dst, int prec, int on_device) {
+    for (int j0 = 0; j0 < k; j0 += c->kmax) {
+        const int kb = std::min(c->kmax, k - j0);
+        const double* s = src + (size_t)j0 * 2 * c->N;
+        const double* dev_src = s;
+        if (!on_device) {
+            CK(cudaMemcpyAsync(c->staging, s, (size_t)kb * c->dbytes, cudaMemcpyHostToDevice, c->stream));
+            dev_src = reinterpret_cast<const double*>(c->staging);
+        }
+        char* d = reinterpret_cast<char*>(dst) + (size_t)j0 * c->N * (prec ? 8 : 16);
+        CK(launch_pack(dev_src, d, c->V, kb, prec, c->stream));
+    }
+    return LQCD_OK;
+}
+
+lqcd_status download(lqcd_ctx* c, const void* src, int prec, int k, double* dst, int on_device) {
+    for (int j0 = 0; j0 < k; j0 += c->kmax) {
+        const int kb = std::min(c->kmax, k - j0);
+        const char* s = reinterpret_cast<const char*>(src) + (size_t)j0 * c->N * (prec ? 8 : 16);
+        double* d = dst + (size_t)j0 * 2 * c->N;
+        if (on_device) {
+            CK(launch_unpack(s, d, c->V, kb, prec, c->stream));
+        } else {
+            CK(launch_unpack(s, reinterpret_cast<double*>(c->staging), c->V, kb, prec, c->stream));
+            CK(cudaMemcpyAsync(d, c->staging, (size_t)kb * c->dbytes, cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
+    return LQCD_OK;
+}
+
+// out_j = A in_j (or A^+, or b_j - A in_j) for nf device fields in precision prec.
+lqcd_status apply_fields(lqcd_ctx* c, int prec, int dagger, int nf, const void* in, size_t in_stride, void* out,
+                         size_t out_stride, const double2* aux) {
+    const void* links = prec ? (const void*)c->links32 : (const void*)c->links64;
+    if (prec && !c->links32) return LQCD_ERR_ARG;
+    std::vector<ApplyJob> jobs(2 * c->kmax);
+    for (int j0 = 0; j0 < nf; j0 += 2 * c->kmax) {
+        const int nb = std::min(2 * c->kmax, nf - j0);
+        for (int j = 0; j < nb; ++j) {
+            jobs[j].in = reinterpret_cast<const char*>(in) + (j0 + j) * in_stride;
+            jobs[j].out = reinterpret_cast<char*>(out) + (j0 + j) * out_stride;
+            jobs[j].aux = aux ? aux + (size_t)(j0 + j) * c->N : nullptr;
+            jobs[j].dagger = dagger;
+        }
+        CK(cudaMemcpyAsync(c->d_jobs, jobs.data(), sizeof(ApplyJob) * nb, cudaMemcpyHostToDevice, c->stream));
+        CK(launch_apply(c->g, links, c->p.kappa, prec, c->d_jobs, nb, aux != nullptr, c->stream));
+        // the job table is reused: wait before overwriting it
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return LQCD_OK;
+}
+
+}  // namespace
+
+extern "C" lqcd_status lqcd_apply(lqcd_ctx* c, int dagger, lqcd_precision prec, int k, const double* in, double* out,
+                                  int on_device) {
+    if (!c || !in || !out || k < 0) return LQCD_ERR_ARG;
+    const int pr = prec == LQCD_MIXED ? 1 : 0;
+    if (pr && !c->links32) return LQCD_ERR_ARG;
+    // work in chunks of kmax fields: input in x_hi_all / x_lo_all, output in rt_all / win
+    for (int j0 = 0; j0 < k; j0 += c->kmax) {
+        const int kb = std::min(c->kmax, k - j0);
+        void* fin = pr ? (void*)c->x_lo_all : (void*)c->x_hi_all;
+        void* fout = pr ? (void*)c->win_all : (void*)c->rt_all;
+        const size_t fb = c->N * (pr ? 8 : 16);
+        lqcd_status s = upload(c, in + (size_t)j0 * 2 * c->N, kb, fin, pr, on_device);
+        if (s != LQCD_OK) return s;
+        s = apply_fields(c, pr, dagger ? 1 : 0, kb, fin, fb, fout, fb, nullptr);
+        if (s != LQCD_OK) return s;
+        s = download(c, fout, pr, kb, out + (size_t)j0 * 2 * c->N, on_device);
+        if (s != LQCD_OK) return s;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
+
+// ============================================================ deflation
+namespace {
+
+// x_hi[j] += U_r H^{-1} U_l^H (b_j - A x_hi[j]) for the first k slots.
+lqcd_status deflate_slots(lqcd_ctx* c, int k) {
+    const int n = c->n_def;
+    if (n == 0 || k == 0) return LQCD_OK;
+    lqcd_status s = apply_fields(c, 0, 0, k, c->x_hi_all, c->dbytes, c->rt_all, c->dbytes, c->b_all);
+    if (s != LQCD_OK) return s;
+    double2* C = c->dsmall;   // n x k, ld k
+    const void* R = c->rt_all;
+    int rp = 0;
+    if (c->kprec) {   // FP32 projections: convert the residuals first
+        CK(launch_convert(c->rt_all, 0, c->x_lo_all, 1, (size_t)k * c->N, c->stream));
+        R = c->x_lo_all;
+        rp = 1;
+    }
+    CK(launch_multidot(n, c->Ul, c->kprec, k, R, rp, c->N, C, k, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_lu_solve(n, c->Hlu, c->n_def_max, c->Hpiv, 0, k, C, k, c->stream));
+    CK(launch_vupdate(n, c->Ur, c->kprec, C, k, k, c->x_hi_all, 0, 0, c->N, c->stream));
+    return LQCD_OK;
+}
+
+lqcd_status refactor(lqcd_ctx* c) {
+    const int n = c->n_def, ld = c->n_def_max;
+    if (n == 0) return LQCD_OK;
+    copy_block_kernel<<<64, 256, 0, c->stream>>>(c->Hdef, ld, c->Hlu, ld, n, n);
+    copy_block_kernel<<<64, 256, 0, c->stream>>>(c->Mdef, ld, c->Mlu, ld, n, n);
+    CK(cudaGetLastError());
+    CK(launch_lu_factor(n, c->Hlu, ld, c->Hpiv, c->dinfo, c->stream));
+    CK(launch_lu_factor(n, c->Mlu, ld, c->Mpiv, c->dinfo + 1, c->stream));
+    return LQCD_OK;
+}
+
+// Append nn new pairs (already stored at columns n_def.. of Ur/Ul) after
+// bi-orthogonalizing them against the existing space (Algorithm Incremental,
+// step 2), scaling to unit norm and growing H = U_l^H A U_r and M = U_l^H U_r.
+// work: at least 2*nn FP64 fields.
+lqcd_status grow_space(lqcd_ctx* c, int nn, double2* work) {
+    const int n = c->n_def, ld = c->n_def_max;
+    nn = std::min(nn, c->n_def_max - n);
+    if (nn <= 0) return LQCD_OK;
+    void* Vn = c->krylov(c->Ur, n);
+    void* Wn = c->krylov(c->Ul, n);
+    const int kp = c->kprec;
+    double2* G = c->dsmall;                        // n x nn
+    double2* G2 = G + (size_t)MAX_SMALL * 16;      // n x nn
+    double2* NV0 = G2 + (size_t)MAX_SMALL * 16;    // nn x nn gram (before)
+    double2* NW0 = NV0 + 256;
+    double2* NV1 = NW0 + 256;
+    double2* NW1 = NV1 + 256;
+    double2* sc = NW1 + 256;                       // nn scales (V), nn (W)
+    double* nrm = reinterpret_cast<double*>(sc + 64);   // 4*nn doubles
+    // norms before the projection
+    CK(launch_multidot(nn, Vn, kp, nn, Vn, kp, c->N, NV0, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_multidot(nn, Wn, kp, nn, Wn, kp, c->N, NW0, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    if (n > 0) {
+        // V' = V - U_r M^{-1} U_l^H V ;  W' = W - U_l M^{-H} U_r^H W
+        CK(launch_multidot(n, c->Ul, kp, nn, Vn, kp, c->N, G, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+        CK(launch_multidot(n, c->Ur, kp, nn, Wn, kp, c->N, G2, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+        CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 0, nn, G, nn, c->stream));
+        CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 1, nn, G2, nn, c->stream));
+        negate_kernel<<<1, 256, 0, c->stream>>>(G, n * nn);
+        negate_kernel<<<1, 256, 0, c->stream>>>(G2, n * nn);
+        CK(cudaGetLastError());
+        CK(launch_vupdate(n, c->Ur, kp, G, nn, nn, Vn, kp, 0, c->N, c->stream));
+        CK(launch_vupdate(n, c->Ul, kp, G2, nn, nn, Wn, kp, 0, c->N, c->stream));
+    }
+    CK(launch_multidot(nn, Vn, kp, nn, Vn, kp, c->N, NV1, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_multidot(nn, Wn, kp, nn, Wn, kp, c->N, NW1, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    inv_norm_kernel<<<1, 64, 0, c->stream>>>(NV0, nn, nn, sc + 32, nrm);
+    inv_norm_kernel<<<1, 64, 0, c->stream>>>(NW0, nn, nn, sc + 32, nrm + nn);
+    inv_norm_kernel<<<1, 64, 0, c->stream>>>(NV1, nn, nn, sc, nrm + 2 * nn);
+    inv_norm_kernel<<<1, 64, 0, c->stream>>>(NW1, nn, nn, sc + nn, nrm + 3 * nn);
+    CK(cudaGetLastError());
+    std::vector<double> hn(4 * nn);
+    CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * 4 * nn, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    // keep pairs whose projected columns retain more than 1e-8 of their norm
+    std::vector<int> keep;
+    for (int i = 0; i < nn; ++i) {
+        const double nv0 = hn[i], nw0 = hn[nn + i], nv = hn[2 * nn + i], nw = hn[3 * nn + i];
+        if (nv > 1e-8 * nv0 && nw > 1e-8 * nw0 && std::isfinite(nv) && std::isfinite(nw)) keep.push_back(i);
+    }
+    // scale to unit norm (device scales), then compact the kept columns
+    CK(launch_scale_fields(nn, Vn, kp, sc, c->N, c->stream));
+    CK(launch_scale_fields(nn, Wn, kp, sc + nn, c->N, c->stream));
+    int kk = 0;
+    for (int i : keep) {
+        if (i != kk) {
+            CK(cudaMemcpyAsync(c->krylov(c->Ur, n + kk), c->krylov(c->Ur, n + i), c->kbytes, cudaMemcpyDeviceToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->krylov(c->Ul, n + kk), c->krylov(c->Ul, n + i), c->kbytes, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        ++kk;
+    }
+    if (kk == 0) return LQCD_OK;
+    // A V' and A^H W' in FP64 (upcast FP32 columns first)
+    double2* AV = work;
+    double2* AW = work + (size_t)kk * c->N;
+    const void* Vin = Vn;
+    const void* Win = Wn;
+    if (kp) {
+        // FP32 columns: upcast into AV / AW, which are then overwritten column by column
+        CK(launch_convert(Vn, 1, AV, 0, (size_t)kk * c->N, c->stream));
+        CK(launch_convert(Wn, 1, AW, 0, (size_t)kk * c->N, c->stream));
+        Vin = AV;
+        Win = AW;
+    }
+    // apply in place is not allowed (stencil reads neighbours): go through staging in chunks
+    for (int j = 0; j < kk; ++j) {
+        lqcd_status s = apply_fields(c, 0, 0, 1, reinterpret_cast<const char*>(Vin) + (size_t)j * (kp ? c->dbytes : c->kbytes),
+                                     0, c->staging, 0, nullptr);
+        if (s != LQCD_OK) return s;
+        CK(cudaMemcpyAsync(AV + (size_t)j * c->N, c->staging, c->dbytes, cudaMemcpyDeviceToDevice, c->stream));
+        s = apply_fields(c, 0, 1, 1, reinterpret_cast<const char*>(Win) + (size_t)j * (kp ? c->dbytes : c->kbytes), 0,
+                         c->staging, 0, nullptr);
+        if (s != LQCD_OK) return s;
+        CK(cudaMemcpyAsync(AW + (size_t)j * c->N, c->staging, c->dbytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    // blocks of H (ld n_def_max): [H, U_l^H AV'; (A^H W')^H U_r, W'^H AV']
+    // and of M: [M, U_l^H V'; W'^H U_r, W'^H V']
+    double2* Hn = c->Hdef;
+    double2* Mn = c->Mdef;
+    if (n > 0) {
+        CK(launch_multidot(n, c->Ul, kp, kk, AV, 0, c->N, Hn + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+        CK(launch_multidot(n, c->Ur, kp, kk, AW, 0, c->N, Hn + (size_t)n * ld, ld, 1, c->mdscratch, c->mdscratch_elems, c->stream));
+        CK(launch_multidot(n, c->Ul, kp, kk, Vn, kp, c->N, Mn + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+        CK(launch_multidot(n, c->Ur, kp, kk, Wn, kp, c->N, Mn + (size_t)n * ld, ld, 1, c->mdscratch, c->mdscratch_elems, c->stream));
+    }
+    CK(launch_multidot(kk, Wn, kp, kk, AV, 0, c->N, Hn + (size_t)n * ld + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_multidot(kk, Wn, kp, kk, Vn, kp, c->N, Mn + (size_t)n * ld + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    c->n_def = n + kk;
+    return refactor(c);
+}
+
+}  // namespace
+
+extern "C" lqcd_status lqcd_deflate(lqcd_ctx* c, int k, const double* b, double* x0, int on_device) {
+    if (!c || !b || !x0 || k < 0) return LQCD_ERR_ARG;
+    if (c->n_def == 0) return LQCD_ERR_STATE;
+    for (int j0 = 0; j0 < k; j0 += c->kmax) {
+        const int kb = std::min(c->kmax, k - j0);
+        lqcd_status s = upload(c, b + (size_t)j0 * 2 * c->N, kb, c->b_all, 0, on_device);
+        if (s != LQCD_OK) return s;
+        s = upload(c, x0 + (size_t)j0 * 2 * c->N, kb, c->x_hi_all, 0, on_device);
+        if (s != LQCD_OK) return s;
+        s = deflate_slots(c, kb);
+        if (s != LQCD_OK) return s;
+        s = download(c, c->x_hi_all, 0, kb, x0 + (size_t)j0 * 2 * c->N, on_device);
+        if (s != LQCD_OK) return s;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
+
+// ============================================================ the solve
+namespace {
+
+// One chunk of CHECK_EVERY iterations for nslots slots (graph body).
+lqcd_status enqueue_chunk(lqcd_ctx* c, int nslots, int windowed) {
+    const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
+    for (int it = 0; it < CHECK_EVERY; ++it) {
+        CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->stream));
+        if (windowed) {
+            CK(launch_restart_coeffs(c->d_state, c->d_ptrs, nslots, c->eigwork, c->stream));
+            CK(launch_window_gemm(c->kprec, 2 * c->nev, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+        }
+        CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+        CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+        CK(launch_bicg_scalars(c->d_state, c->d_ptrs, nslots, c->stream));
+        CK(launch_bicg_direction(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+    }
+    return LQCD_OK;
+}
+
+lqcd_status run_chunk(lqcd_ctx* c, int nslots, int windowed) {
+    cudaGraphExec_t& ge = c->graphs[nslots][windowed];
+    if (!ge) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        lqcd_status s = enqueue_chunk(c, nslots, windowed);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (s != LQCD_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+        if (e != cudaSuccess) { set_error("cudaStreamEndCapture", e); return LQCD_ERR_CUDA; }
+        e = cudaGraphInstantiate(&ge, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { ge = nullptr; set_error("cudaGraphInstantiate", e); return LQCD_ERR_CUDA; }
+    }
+    CK(cudaGraphLaunch(ge, c->stream));
+    return LQCD_OK;
+}
+
+// Solve the right-hand sides already in slots 0..k-1 (b_all, x_hi_all);
+// windowed = eigBiCG window on. tol_override > 0 replaces the tolerance.
+lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol) {
+    for (int s = 0; s < c->kmax; ++s) {
+        SlotState& st = c->h_state[s];
+        memset(&st, 0, sizeof(SlotState));
+        st.status = s < k ? ST_RUNNING : ST_IDLE;
+        st.tol = tol;
+        st.maxiter = c->p.maxiter;
+        st.delta = c->kprec ? c->p.delta : 0.0;
+        st.m = windowed ? c->m : 0;
+        st.nev = c->nev;
+    }
+    CK(cudaMemcpyAsync(c->d_state, c->h_state, sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
+    // r0 = b - A x0 (FP64), then the Krylov start vectors
+    lqcd_status s = apply_fields(c, 0, 0, k, c->x_hi_all, c->dbytes, c->rt_all, c->dbytes, c->b_all);
+    if (s != LQCD_OK) return s;
+    CK(launch_bicg_start(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
+    while (true) {
+        CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SlotState) * k, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        bool any = false;
+        for (int j = 0; j < k; ++j) any = any || c->h_state[j].status == ST_RUNNING;
+        if (!any) break;
+        s = run_chunk(c, k, windowed);
+        if (s != LQCD_OK) return s;
+    }
+    CK(launch_bicg_finish(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
+    CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SlotState) * k, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
+
+// After an eigBiCG batch: final Ritz vectors of every slot, appended in slot order.
+lqcd_status grow_from_windows(lqcd_ctx* c, int k) {
+    for (int s = 0; s < k; ++s) {
+        c->last_vs[s] = c->h_state[s].vs;
+        c->last_restarts[s] = c->h_state[s].restarts;
+        c->last_ritz[s].clear();
+    }
+    c->last_window_valid = 1;
+    for (int s = 0; s < k; ++s) {
+        const SlotState& st = c->h_state[s];
+        if (st.status != ST_CONVERGED) continue;
+        const int vs = st.vs;
+        const int nsel = std::min(c->nev, vs);
+        if (nsel == 0) continue;
+        const int room = c->n_def_max - c->n_def;
+        if (room <= 0) break;
+        const int take = std::min(nsel, room);
+        double2* Yc = c->dsmall + (size_t)MAX_SMALL * MAX_SMALL * 2;
+        double2* Zc = Yc + (size_t)MAX_M * MAX_M;
+        double2* lam = Zc + (size_t)MAX_M * MAX_M;
+        int* nout = c->dinfo + 8;
+        CK(launch_final_ritz(c->d_state, c->d_ptrs, s, Yc, Zc, lam, nout, c->eigwork, c->stream));
+        std::vector<double2> hl(nsel);
+        CK(cudaMemcpyAsync(hl.data(), lam, sizeof(double2) * nsel, cudaMemcpyDeviceToHost, c->stream));
+        const SlotPtrs& P = c->h_ptrs[s];
+        // U = V Yc, Q = W Zc  into the next eigenspace columns (first 'take' of nsel)
+        CK(launch_vupdate(vs, P.V, c->kprec, Yc, nsel, take, c->krylov(c->Ur, c->n_def), c->kprec, 1, c->N, c->stream));
+        CK(launch_vupdate(vs, P.W, c->kprec, Zc, nsel, take, c->krylov(c->Ul, c->n_def), c->kprec, 1, c->N, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->last_ritz[s] = hl;
+        // FP64 work fields for A V', A^H W': this slot's window (>= 2*take FP64 fields)
+        double2* work = reinterpret_cast<double2*>(P.V);
+        if ((size_t)2 * (c->m + 1) * c->kbytes < (size_t)2 * take * c->dbytes) work = c->rt_all;  // tiny windows
+        lqcd_status r = grow_space(c, take, work);
+        if (r != LQCD_OK) return r;
+        c->eig_rhs_done += 1;
+    }
+    return LQCD_OK;
+}
+
+lqcd_status status_of(const SlotState& st) {
+    switch (st.status) {
+        case ST_CONVERGED: return LQCD_OK;
+        case ST_BREAKDOWN: return LQCD_ERR_BREAKDOWN;
+        case ST_NOCONV: return LQCD_ERR_NOCONV;
+        default: return LQCD_OK;
+    }
+}
+
+}  // namespace
+
+extern "C" lqcd_status lqcd_solve(lqcd_ctx* c, int k, const double* b, double* x, int on_device, lqcd_mode mode,
+                                  lqcd_solve_info* info) {
+    if (!c || k < 0 || (k > 0 && (!b || !x))) return LQCD_ERR_ARG;
+    if (mode < LQCD_MODE_AUTO || mode > LQCD_MODE_PLAIN) return LQCD_ERR_ARG;
+    lqcd_status worst = LQCD_OK;
+    for (int j0 = 0; j0 < k; j0 += c->kmax) {
+        auto t0 = std::chrono::steady_clock::now();
+        const int kb = std::min(c->kmax, k - j0);
+        lqcd_mode md = mode;
+        if (md == LQCD_MODE_AUTO) md = c->eig_rhs_done < c->p.n1 ? LQCD_MODE_EIGBICG : LQCD_MODE_DEFLATED;
+        lqcd_status s = upload(c, b + (size_t)j0 * 2 * c->N, kb, c->b_all, 0, on_device);
+        if (s != LQCD_OK) return s;
+        s = upload(c, x + (size_t)j0 * 2 * c->N, kb, c->x_hi_all, 0, on_device);
+        if (s != LQCD_OK) return s;
+        int outer = 0;
+        if (md != LQCD_MODE_PLAIN && c->n_def > 0) {
+            s = deflate_slots(c, kb);
+            if (s != LQCD_OK) return s;
+        }
+        std::vector<SlotState> first;
+        const bool windowed = md == LQCD_MODE_EIGBICG;
+        if (windowed) c->last_window_valid = 0;
+        if (md == LQCD_MODE_DEFLATED && c->p.deftol > c->p.tol && c->n_def > 0) {
+            // DefTol restart: solve to deftol, re-deflate, solve to tol
+            s = solve_slots(c, kb, 0, c->p.deftol);
+            if (s != LQCD_OK) return s;
+            first.assign(c->h_state, c->h_state + kb);
+            s = deflate_slots(c, kb);
+            if (s != LQCD_OK) return s;
+            outer = 1;
+        }
+        s = solve_slots(c, kb, windowed ? 1 : 0, c->p.tol);
+        if (s != LQCD_OK) return s;
+        std::vector<SlotState> fin(c->h_state, c->h_state + kb);
+        if (windowed) {
+            s = grow_from_windows(c, kb);
+            if (s != LQCD_OK) return s;
+        }
+        s = download(c, c->x_hi_all, 0, kb, x + (size_t)j0 * 2 * c->N, on_device);
+        if (s != LQCD_OK) return s;
+        CK(cudaStreamSynchronize(c->stream));
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int j = 0; j < kb; ++j) {
+            const SlotState& st = fin[j];
+            lqcd_status sj = status_of(st);
+            if (sj == LQCD_OK && st.bnorm > 0 && st.true_rnorm > c->p.tol * st.bnorm) sj = LQCD_ERR_NOCONV;
+            if (sj != LQCD_OK && worst == LQCD_OK) worst = sj;
+            if (info) {
+                lqcd_solve_info& in = info[j0 + j];
+                in.iters = st.iter + (first.empty() ? 0 : first[j].iter);
+                in.matvecs = st.matvecs + (first.empty() ? 0 : first[j].matvecs);
+                in.restarts = st.restarts;
+                in.reliable_updates = st.ru_count + (first.empty() ? 0 : first[j].ru_count);
+                in.outer_steps = outer;
+                in.true_resid = st.bnorm > 0 ? st.true_rnorm / st.bnorm : 0.0;
+                in.seconds = secs;
+                in.mode_used = md;
+            }
+        }
+    }
+    return worst;
+}
+
+// ============================================================ eigenspace I/O
+extern "C" lqcd_status lqcd_eigspace_get(lqcd_ctx* c, double* Ur, double* Ul, double* H) {
+    if (!c) return LQCD_ERR_ARG;
+    const int n = c->n_def;
+    if (Ur) { lqcd_status s = download(c, c->Ur, c->kprec, n, Ur, 0); if (s != LQCD_OK) return s; }
+    if (Ul) { lqcd_status s = download(c, c->Ul, c->kprec, n, Ul, 0); if (s != LQCD_OK) return s; }
+    if (H && n > 0) {
+        CK(cudaMemcpy2DAsync(H, sizeof(double2) * n, c->Hdef, sizeof(double2) * c->n_def_max, sizeof(double2) * n, n,
+                             cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_eigspace_set(lqcd_ctx* c, int n, const double* Ur, const double* Ul) {
+    if (!c || n < 0 || n > c->n_def_max) return LQCD_ERR_ARG;
+    if (n > 0 && (!Ur || !Ul)) return LQCD_ERR_ARG;
+    c->n_def = 0;
+    if (n == 0) return LQCD_OK;
+    lqcd_status s = upload(c, Ur, n, c->Ur, c->kprec, 0);
+    if (s != LQCD_OK) return s;
+    s = upload(c, Ul, n, c->Ul, c->kprec, 0);
+    if (s != LQCD_OK) return s;
+    // H = U_l^H A U_r, M = U_l^H U_r in FP64, in chunks of kmax columns
+    const int ld = c->n_def_max;
+    for (int j0 = 0; j0 < n; j0 += c->kmax) {
+        const int kb = std::min(c->kmax, n - j0);
+        const void* src = c->krylov(c->Ur, j0);
+        const void* in = src;
+        if (c->kprec) {
+            CK(launch_convert(src, 1, c->x_hi_all, 0, (size_t)kb * c->N, c->stream));
+            in = c->x_hi_all;
+        }
+        s = apply_fields(c, 0, 0, kb, in, c->kprec ? c->dbytes : c->kbytes, c->rt_all, c->dbytes, nullptr);
+        if (s != LQCD_OK) return s;
+        CK(launch_multidot(n, c->Ul, c->kprec, kb, c->rt_all, 0, c->N, c->Hdef + j0, ld, 0, c->mdscratch,
+                           c->mdscratch_elems, c->stream));
+        CK(launch_multidot(n, c->Ul, c->kprec, kb, src, c->kprec, c->N, c->Mdef + j0, ld, 0, c->mdscratch,
+                           c->mdscratch_elems, c->stream));
+    }
+    c->n_def = n;
+    s = refactor(c);
+    if (s != LQCD_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
+
+// ============================================================ Rayleigh-Ritz
+extern "C" lqcd_status lqcd_eigs(lqcd_ctx* c, int* n_inout, double* evals, double* evecs_r, double* evecs_l,
+                                 double* resid) {
+    if (!c || !n_inout || !evals) return LQCD_ERR_ARG;
+    const int n = c->n_def;
+    if (n == 0) return LQCD_ERR_STATE;
+    const int nout = std::min(*n_inout, n);
+    const int ld = c->n_def_max;
+    // G = M^{-1} H  (n x n, ld n) ; eig(G) -> lam, Y, Zhat ; left vectors z = M^{-H} zhat
+    double2* G = c->dsmall;
+    double2* Y = G + (size_t)n * n;
+    double2* Z = Y + (size_t)n * n;
+    double2* lam = Z + (size_t)n * n;
+    copy_block_kernel<<<64, 256, 0, c->stream>>>(c->Hdef, ld, G, n, n, n);
+    CK(cudaGetLastError());
+    CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 0, n, G, n, c->stream));
+    CK(launch_small_eig(n, G, n, n, lam, Y, Z, n, c->dinfo + 16, c->eigwork, c->stream));
+    CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 1, n, Z, n, c->stream));
+    std::vector<double2> hl(n);
+    CK(cudaMemcpyAsync(hl.data(), lam, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < nout; ++i) { evals[2 * i] = hl[i].x; evals[2 * i + 1] = hl[i].y; }
+    // vectors in chunks of kmax: u = U_r y (FP64 in x_hi_all), w = U_l z (rt_all)
+    std::vector<double> hres(nout, 0.0);
+    for (int j0 = 0; j0 < nout; j0 += c->kmax) {
+        const int kb = std::min(c->kmax, nout - j0);
+        CK(launch_vupdate(n, c->Ur, c->kprec, Y + j0, n, kb, c->x_hi_all, 0, 1, c->N, c->stream));
+        if (evecs_r) {
+            lqcd_status s = download(c, c->x_hi_all, 0, kb, evecs_r + (size_t)j0 * 2 * c->N, 0);
+            if (s != LQCD_OK) return s;
+        }
+        if (evecs_l) {
+            CK(launch_vupdate(n, c->Ul, c->kprec, Z + j0, n, kb, c->rt_all, 0, 1, c->N, c->stream));
+            lqcd_status s = download(c, c->rt_all, 0, kb, evecs_l + (size_t)j0 * 2 * c->N, 0);
+            if (s != LQCD_OK) return s;
+        }
+        if (resid) {
+            // r_j = A u_j - lam_j u_j ; |r_j| / |u_j|
+            lqcd_status s = apply_fields(c, 0, 0, kb, c->x_hi_all, c->dbytes, c->rt_all, c->dbytes, nullptr);
+            if (s != LQCD_OK) return s;
+            double2* D = c->dsmall + (size_t)MAX_SMALL * MAX_SMALL * 4;
+            std::vector<double2> hd((size_t)kb * kb, make_double2(0, 0));
+            for (int j = 0; j < kb; ++j) hd[(size_t)j * kb + j] = make_double2(-hl[j0 + j].x, -hl[j0 + j].y);
+            CK(cudaMemcpyAsync(D, hd.data(), sizeof(double2) * kb * kb, cudaMemcpyHostToDevice, c->stream));
+            CK(launch_vupdate(kb, c->x_hi_all, 0, D, kb, kb, c->rt_all, 0, 0, c->N, c->stream));
+            double2* gr = D + 256;
+            double2* gu = gr + 256;
+            CK(launch_multidot(kb, c->rt_all, 0, kb, c->rt_all, 0, c->N, gr, kb, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+            CK(launch_multidot(kb, c->x_hi_all, 0, kb, c->x_hi_all, 0, c->N, gu, kb, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+            std::vector<double2> hr((size_t)kb * kb), hu((size_t)kb * kb);
+            CK(cudaMemcpyAsync(hr.data(), gr, sizeof(double2) * kb * kb, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(hu.data(), gu, sizeof(double2) * kb * kb, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            for (int j = 0; j < kb; ++j)
+                hres[j0 + j] = std::sqrt(std::max(hr[(size_t)j * kb + j].x, 0.0)) / std::sqrt(std::max(hu[(size_t)j * kb + j].x, 1e-300));
+        }
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    if (resid)
+        for (int i = 0; i < nout; ++i) resid[i] = hres[i];
+    *n_inout = nout;
+    return LQCD_OK;
+}
+
+// ============================================================ inspection
+extern "C" lqcd_status lqcd_last_window(lqcd_ctx* c, int slot, int* vs, double* H, double* ritz, int* restarts) {
+    if (!c || slot < 0 || slot >= c->kmax) return LQCD_ERR_ARG;
+    if (!c->last_window_valid) return LQCD_ERR_STATE;
+    const int nvs = c->last_vs[slot];
+    if (vs) *vs = nvs;
+    if (restarts) *restarts = c->last_restarts[slot];
+    if (H) {
+        std::vector<double2> h((size_t)c->m * c->m);
+        CK(cudaMemcpy(h.data(), c->h_ptrs[slot].H, sizeof(double2) * c->m * c->m, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < nvs; ++i)
+            for (int j = 0; j < nvs; ++j) {
+                H[2 * ((size_t)i * nvs + j)] = h[(size_t)i * c->m + j].x;
+                H[2 * ((size_t)i * nvs + j) + 1] = h[(size_t)i * c->m + j].y;
+            }
+    }
+    if (ritz) {
+        const auto& r = c->last_ritz[slot];
+        for (size_t i = 0; i < r.size(); ++i) { ritz[2 * i] = r[i].x; ritz[2 * i + 1] = r[i].y; }
+    }
+    return LQCD_OK;
+}
+
+// ============================================================ test hooks
+extern "C" lqcd_status lqcd_small_eig(int n, const double* C, double* evals, double* Yout, double* Zout) {
+    if (n < 1 || n > MAX_SMALL || !C || !evals) return LQCD_ERR_ARG;
+    double2 *dA = nullptr, *dl = nullptr, *dY = nullptr, *dZ = nullptr, *dw = nullptr;
+    int* dinfo = nullptr;
+    size_t nn = (size_t)n * n;
+    lqcd_status ret = LQCD_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&dA, nn * 16)) != cudaSuccess || (e = cudaMalloc(&dl, n * 16)) != cudaSuccess ||
+        (e = cudaMalloc(&dY, nn * 16)) != cudaSuccess || (e = cudaMalloc(&dZ, nn * 16)) != cudaSuccess ||
+        (e = cudaMalloc(&dw, eig_work_elems() * 16)) != cudaSuccess || (e = cudaMalloc(&dinfo, 16)) != cudaSuccess) {
+        set_error("cudaMalloc", e);
+        ret = LQCD_ERR_OOM;
+    }
+    int info = 0;
+    if (ret == LQCD_OK) {
+        e = cudaMemcpy(dA, C, nn * 16, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_small_eig(n, dA, n, n, dl, dY, dZ, n, dinfo, dw, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(evals, dl, n * 16, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && Yout) e = cudaMemcpy(Yout, dY, nn * 16, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && Zout) e = cudaMemcpy(Zout, dZ, nn * 16, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { set_error("small eig", e); ret = LQCD_ERR_CUDA; }
+        else if (info) { g_last_error = "QR iteration did not converge"; ret = LQCD_ERR_NOCONV; }
+    }
+    cudaFree(dA); cudaFree(dl); cudaFree(dY); cudaFree(dZ); cudaFree(dw); cudaFree(dinfo);
+    return ret;
+}
+
+extern "C" lqcd_status lqcd_restart_coefficients(int m, int nev, const double* H, int* r, double* Yc, double* Zc,
+                                                 double* lam) {
+    if (m < 3 || m > MAX_M || nev < 1 || 2 * nev >= m || !H || !r) return LQCD_ERR_ARG;
+    double2 *dH = nullptr, *dY = nullptr, *dZ = nullptr, *dl = nullptr, *dw = nullptr;
+    int* di = nullptr;
+    lqcd_status ret = LQCD_OK;
+    cudaError_t e;
+    const size_t cs = (size_t)m * 2 * nev;
+    if ((e = cudaMalloc(&dH, (size_t)m * m * 16)) != cudaSuccess || (e = cudaMalloc(&dY, cs * 16)) != cudaSuccess ||
+        (e = cudaMalloc(&dZ, cs * 16)) != cudaSuccess || (e = cudaMalloc(&dl, 2 * nev * 16)) != cudaSuccess ||
+        (e = cudaMalloc(&dw, eig_work_elems() * 16)) != cudaSuccess || (e = cudaMalloc(&di, 16)) != cudaSuccess) {
+        set_error("cudaMalloc", e);
+        ret = LQCD_ERR_OOM;
+    }
+    int hi[2] = {0, 0};
+    if (ret == LQCD_OK) {
+        e = cudaMemcpy(dH, H, (size_t)m * m * 16, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_restart_coeffs_single(m, nev, dH, di, dY, dZ, dl, di + 1, dw, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(hi, di, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && Yc) e = cudaMemcpy(Yc, dY, cs * 16, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && Zc) e = cudaMemcpy(Zc, dZ, cs * 16, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && lam) e = cudaMemcpy(lam, dl, 2 * nev * 16, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { set_error("restart coefficients", e); ret = LQCD_ERR_CUDA; }
+        else {
+            *r = hi[0];
+            if (hi[1]) { g_last_error = "QR iteration did not converge"; ret = LQCD_ERR_NOCONV; }
+        }
+    }
+    cudaFree(dH); cudaFree(dY); cudaFree(dZ); cudaFree(dl); cudaFree(dw); cudaFree(di);
+    return ret;
+}

@@ -1,0 +1,319 @@
+"""Python binding of the C ABI in ``include/lqcd.h`` (ctypes).
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of
+``liblqcd.so``. Fields are complex128 arrays of length ``12*V`` in the order
+``[site][spin][colour]`` (site ``x + Lx*(y + Ly*(z + Lz*t))``); a batch of
+``k`` fields is a ``(k, 12*V)`` array. Host arrays (numpy, CPU torch) are
+passed as host pointers; CUDA torch tensors are passed as device pointers and
+must be contiguous complex128 on the library's device.
+
+The library must have been built (``paper_0911_2285_gb300.build.build()``);
+there is no fallback: a missing library raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblqcd.so")
+
+# lqcd_status
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOCONV, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_STATE = range(8)
+FP64, MIXED = 0, 1
+MODE_AUTO, MODE_EIGBICG, MODE_DEFLATED, MODE_PLAIN = 0, 1, 2, 3
+_MODES = {"auto": MODE_AUTO, "eigbicg": MODE_EIGBICG, "deflated": MODE_DEFLATED, "plain": MODE_PLAIN}
+_PREC = {"fp64": FP64, "mixed": MIXED}
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("dims", C.c_int * 4),
+        ("kappa", C.c_double),
+        ("nev", C.c_int),
+        ("m", C.c_int),
+        ("n1", C.c_int),
+        ("tol", C.c_double),
+        ("maxiter", C.c_int),
+        ("precision", C.c_int),
+        ("deftol", C.c_double),
+        ("k_max", C.c_int),
+        ("hbm_budget_bytes", C.c_size_t),
+        ("n_def_max", C.c_int),
+        ("delta", C.c_double),
+    ]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int),
+        ("matvecs", C.c_int),
+        ("restarts", C.c_int),
+        ("reliable_updates", C.c_int),
+        ("outer_steps", C.c_int),
+        ("true_resid", C.c_double),
+        ("seconds", C.c_double),
+        ("mode_used", C.c_int),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class LQCDError(RuntimeError):
+    def __init__(self, status, where, msg=""):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)}" + (f" ({msg})" if msg else ""))
+
+
+_lib = None
+
+
+def lib():
+    """The loaded ``liblqcd.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_0911_2285_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.lqcd_eigbicg_init.argtypes = [C.POINTER(vp), C.POINTER(Params), vp, vp]
+        L.lqcd_solve.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.POINTER(SolveInfo)]
+        L.lqcd_deflate.argtypes = [vp, C.c_int, vp, vp, C.c_int]
+        L.lqcd_eigs.argtypes = [vp, ip, vp, vp, vp, vp]
+        L.lqcd_apply.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, C.c_int]
+        L.lqcd_eigspace_size.argtypes = [vp]
+        L.lqcd_eigspace_size.restype = C.c_int
+        L.lqcd_eigspace_get.argtypes = [vp, vp, vp, vp]
+        L.lqcd_eigspace_set.argtypes = [vp, C.c_int, vp, vp]
+        L.lqcd_last_window.argtypes = [vp, C.c_int, ip, vp, vp, ip]
+        L.lqcd_small_eig.argtypes = [C.c_int, vp, vp, vp, vp]
+        L.lqcd_restart_coefficients.argtypes = [C.c_int, C.c_int, vp, ip, vp, vp, vp]
+        L.lqcd_status_str.argtypes = [C.c_int]
+        L.lqcd_status_str.restype = C.c_char_p
+        L.lqcd_last_error.restype = C.c_char_p
+        L.lqcd_destroy.argtypes = [vp]
+        for name in ("lqcd_eigbicg_init", "lqcd_solve", "lqcd_deflate", "lqcd_eigs", "lqcd_apply",
+                     "lqcd_eigspace_get", "lqcd_eigspace_set", "lqcd_last_window", "lqcd_small_eig",
+                     "lqcd_restart_coefficients"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def status_str(s):
+    return lib().lqcd_status_str(int(s)).decode()
+
+
+def last_error():
+    return lib().lqcd_last_error().decode()
+
+
+def _check(status, where, allow=()):
+    if status != OK and status not in allow:
+        raise LQCDError(status, where, last_error())
+    return status
+
+
+def _ptr(a, n_expected=None):
+    """(pointer, on_device) of a contiguous complex128 array or tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.complex128 or not a.is_contiguous():
+                raise TypeError("torch fields must be contiguous complex128")
+            if n_expected is not None and a.numel() != n_expected:
+                raise ValueError(f"expected {n_expected} complex numbers, got {a.numel()}")
+            return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    except ImportError:  # pragma: no cover - torch is optional for the host path
+        pass
+    if not isinstance(a, np.ndarray) or a.dtype != np.complex128 or not a.flags.c_contiguous:
+        raise TypeError("fields must be C-contiguous complex128 numpy arrays or torch tensors")
+    if n_expected is not None and a.size != n_expected:
+        raise ValueError(f"expected {n_expected} complex numbers, got {a.size}")
+    return C.c_void_p(a.ctypes.data), 0
+
+
+class Solver:
+    """One gauge field + parameter set (an ``lqcd_ctx``)."""
+
+    def __init__(self, links, dims, kappa, nev=10, m=40, n1=4, tol=1e-10, maxiter=5000,
+                 precision="mixed", deftol=0.0, k_max=0, hbm_budget_bytes=0, n_def_max=0,
+                 delta=0.0, stream=None):
+        links = np.ascontiguousarray(links, dtype=np.complex128)
+        self.dims = tuple(int(d) for d in dims)
+        self.volume = int(np.prod(self.dims))
+        self.n = 12 * self.volume
+        if links.size != 4 * self.volume * 9:
+            raise ValueError("links must hold 4*V*9 complex numbers")
+        p = Params()
+        for i, d in enumerate(self.dims):
+            p.dims[i] = d
+        p.kappa = kappa
+        p.nev, p.m, p.n1 = nev, m, n1
+        p.tol, p.maxiter = tol, maxiter
+        p.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        p.deftol, p.k_max = deftol, k_max
+        p.hbm_budget_bytes = hbm_budget_bytes
+        p.n_def_max = n_def_max
+        p.delta = delta
+        self.params = p
+        self.precision = precision
+        h = C.c_void_p()
+        st = lib().lqcd_eigbicg_init(C.byref(h), C.byref(p), C.c_void_p(links.ctypes.data),
+                                     C.c_void_p(stream) if stream else None)
+        _check(st, "lqcd_eigbicg_init")
+        self._h = h
+        self.kmax = k_max or 8
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lqcd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- calls
+    def solve(self, b, x0=None, mode="auto", raise_on_fail=True):
+        """Solve ``A x = b`` for a batch; returns ``(x, infos, status)``."""
+        b = _as_batch(b, self.n)
+        k = b.shape[0]
+        if x0 is None:
+            x = _zeros_like(b)
+        else:
+            x = _as_batch(x0, self.n)
+            x = x.clone() if hasattr(x, "clone") else x.copy()
+        pb, db = _ptr(b, k * self.n)
+        px, dx = _ptr(x, k * self.n)
+        if db != dx:
+            raise ValueError("b and x must both be host or both be device arrays")
+        infos = (SolveInfo * max(k, 1))()
+        st = lib().lqcd_solve(self._h, k, pb, px, db, _MODES[mode] if isinstance(mode, str) else int(mode), infos)
+        if raise_on_fail:
+            _check(st, "lqcd_solve")
+        return x, [infos[i].as_dict() for i in range(k)], st
+
+    def deflate(self, b, x0):
+        b = _as_batch(b, self.n)
+        x = _as_batch(x0, self.n)
+        x = x.clone() if hasattr(x, "clone") else x.copy()
+        pb, db = _ptr(b)
+        px, dx = _ptr(x)
+        _check(lib().lqcd_deflate(self._h, b.shape[0], pb, px, db), "lqcd_deflate")
+        return x
+
+    def apply(self, v, dagger=False, precision="fp64"):
+        v = _as_batch(v, self.n)
+        out = _zeros_like(v)
+        pv, dv = _ptr(v)
+        po, do = _ptr(out)
+        _check(lib().lqcd_apply(self._h, int(dagger), _PREC[precision], v.shape[0], pv, po, dv), "lqcd_apply")
+        return out
+
+    def eigs(self, n=None, vectors=False):
+        """Rayleigh-Ritz eigenpairs of the accumulated eigenspace."""
+        size = self.eigspace_size()
+        n = size if n is None else min(n, size)
+        cnt = C.c_int(n)
+        ev = np.zeros(max(n, 1), dtype=np.complex128)
+        res = np.zeros(max(n, 1), dtype=np.float64)
+        ur = np.zeros((n, self.n), dtype=np.complex128) if vectors else None
+        ul = np.zeros((n, self.n), dtype=np.complex128) if vectors else None
+        st = lib().lqcd_eigs(self._h, C.byref(cnt), C.c_void_p(ev.ctypes.data),
+                             C.c_void_p(ur.ctypes.data) if vectors else None,
+                             C.c_void_p(ul.ctypes.data) if vectors else None, C.c_void_p(res.ctypes.data))
+        _check(st, "lqcd_eigs")
+        k = cnt.value
+        return ev[:k], res[:k], (ur[:k] if vectors else None), (ul[:k] if vectors else None)
+
+    def eigspace_size(self):
+        return lib().lqcd_eigspace_size(self._h)
+
+    def eigspace_get(self):
+        n = self.eigspace_size()
+        ur = np.zeros((n, self.n), dtype=np.complex128)
+        ul = np.zeros((n, self.n), dtype=np.complex128)
+        h = np.zeros((n, n), dtype=np.complex128)
+        if n:
+            _check(lib().lqcd_eigspace_get(self._h, C.c_void_p(ur.ctypes.data), C.c_void_p(ul.ctypes.data),
+                                           C.c_void_p(h.ctypes.data)), "lqcd_eigspace_get")
+        return ur, ul, h
+
+    def eigspace_set(self, ur, ul):
+        ur = np.ascontiguousarray(ur, dtype=np.complex128).reshape(-1, self.n)
+        ul = np.ascontiguousarray(ul, dtype=np.complex128).reshape(-1, self.n)
+        if ur.shape != ul.shape:
+            raise ValueError("Ur and Ul must have the same shape")
+        _check(lib().lqcd_eigspace_set(self._h, ur.shape[0], C.c_void_p(ur.ctypes.data),
+                                       C.c_void_p(ul.ctypes.data)), "lqcd_eigspace_set")
+
+    def last_window(self, slot=0):
+        m = self.params.m
+        vs = C.c_int()
+        rs = C.c_int()
+        h = np.zeros(m * m, dtype=np.complex128)
+        ritz = np.zeros(self.params.nev, dtype=np.complex128)
+        _check(lib().lqcd_last_window(self._h, slot, C.byref(vs), C.c_void_p(h.ctypes.data),
+                                      C.c_void_p(ritz.ctypes.data), C.byref(rs)), "lqcd_last_window")
+        v = vs.value
+        return h[: v * v].reshape(v, v), ritz[: min(v, self.params.nev)], rs.value
+
+
+def _as_batch(a, n):
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return a.reshape(-1, n)
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a.reshape(-1, n)
+
+
+def _zeros_like(a):
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return torch.zeros_like(a)
+    except ImportError:  # pragma: no cover
+        pass
+    return np.zeros_like(a)
+
+
+def small_eig(c):
+    """Device eigen-solver on a small dense matrix: ``(lam, Y, Z)``, smallest |lambda| first."""
+    c = np.ascontiguousarray(c, dtype=np.complex128)
+    n = c.shape[0]
+    lam = np.zeros(n, dtype=np.complex128)
+    y = np.zeros((n, n), dtype=np.complex128)
+    z = np.zeros((n, n), dtype=np.complex128)
+    _check(lib().lqcd_small_eig(n, C.c_void_p(c.ctypes.data), C.c_void_p(lam.ctypes.data),
+                                C.c_void_p(y.ctypes.data), C.c_void_p(z.ctypes.data)), "lqcd_small_eig")
+    return lam, y, z
+
+
+def restart_coefficients(h, nev):
+    """Device Algorithm BiCG-eigen (coefficient part): ``(Yc, Zc, lam)``."""
+    h = np.ascontiguousarray(h, dtype=np.complex128)
+    m = h.shape[0]
+    r = C.c_int()
+    yc = np.zeros((m, 2 * nev), dtype=np.complex128)
+    zc = np.zeros((m, 2 * nev), dtype=np.complex128)
+    lam = np.zeros(2 * nev, dtype=np.complex128)
+    _check(lib().lqcd_restart_coefficients(m, nev, C.c_void_p(h.ctypes.data), C.byref(r),
+                                           C.c_void_p(yc.ctypes.data), C.c_void_p(zc.ctypes.data),
+                                           C.c_void_p(lam.ctypes.data)), "lqcd_restart_coefficients")
+    k = r.value
+    return yc[:, :k].copy(), zc[:, :k].copy(), lam[:k].copy()

@@ -1,0 +1,59 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point of
+include/lqcd.h; argument validation happens before any device call (CPU only)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_0911_2285_gb300.build import build
+    return build()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lqcd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lqcd_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("lqcd_eigbicg_init", "lqcd_solve", "lqcd_deflate", "lqcd_eigs", "lqcd_apply", "lqcd_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (lqcd_[a-z_0-9]+)", out))
+    missing = [n for n in declared_symbols() if n not in exported]
+    assert not missing, missing
+    lib = C.CDLL(libpath)
+    for n in declared_symbols():
+        assert hasattr(lib, n)
+
+
+def test_status_strings(libpath):
+    from paper_0911_2285_gb300 import lqcd as L
+    assert L.status_str(L.OK) == "ok"
+    assert "argument" in L.status_str(L.ERR_ARG)
+
+
+@pytest.mark.parametrize("bad", [dict(m=16, nev=8), dict(dims=(1, 4, 4, 4)), dict(tol=0.0), dict(k_max=9),
+                                 dict(kappa=-1.0), dict(m=80), dict(n_def_max=200)])
+def test_init_rejects_bad_parameters_without_touching_the_device(libpath, bad):
+    import numpy as np
+    from paper_0911_2285_gb300 import lqcd as L
+    args = dict(dims=(4, 4, 4, 4), kappa=0.12, nev=8, m=24, tol=1e-10)
+    args.update(bad)
+    dims = args.pop("dims")
+    v = int(np.prod(dims))
+    links = np.zeros(max(v, 1) * 36, dtype=np.complex128)
+    with pytest.raises(L.LQCDError) as e:
+        L.Solver(links if v > 0 else links, dims, **args)
+    assert e.value.status == L.ERR_ARG
