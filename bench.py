@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark: right-hand sides solved per second to an FP64 true residual of 1e-10.
+
+Workload (default): the 24^3x64 Wilson-Dirac problem (10.6M complex unknowns,
+random SU(3) links eps = 0.3, kappa = 0.1245), 64 complex Z2 sources, solved by
+Incremental eigBiCG (paper Sec. 2): the first 8 sources with eigBiCG
+(nev = 10, m = 60, one batch of k = 8 per operator launch) building an
+80-vector eigenspace, the other 56 with deflated BiCG in batches of 8; FP32
+Krylov vectors and links (third-row reconstruction) with FP64 reliable updates.
+One "step" is that whole job from an empty eigenspace. Every solution is
+checked against the FP64 true-residual tolerance inside the library.
+
+Printed JSON line (rank 0): the metric, ``e2e`` (the same job through the C ABI
+with pinned host buffers, copies inside the timed region), a ``roofline`` for
+the dominant kernel (the batched operator pair A p / A^+ phat), the plain FP64
+single-RHS BiCG rate on the same GPU, the CPU oracle rate as ``cpu_baseline``,
+and the SM clocks sampled during the timed region.
+
+``--impl reference`` times the CPU oracle on the same workload (bounded sample).
+Multi-GPU (torchrun): every rank solves its own copy of the job (independent
+problems, no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RHS solved/sec to FP64 resid 1e-10 (deflated batched vs plain BiCG); D_hop GB/s"
+HBM_BYTES_PER_SITE_PAIR = {"links": 4 * 48, "per_rhs": 4 * 96}   # FP32: links once, p, phat in, Ap, Ahp out
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="24^3x64")
+    ap.add_argument("--n-rhs", type=int, default=0, help="sources per step (default: the workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--plain-rhs", type=int, default=2, help="sources timed for the plain FP64 BiCG rate")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- profiles
+def recorded_traffic(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    src = source_hash()
+    if vals.get("source_sha256") != src:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "dslash.cuh", "common.cuh", "solver.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_0911_2285_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------ distributed
+def dist_setup(n):
+    if n <= 1 or "RANK" not in os.environ:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return dist.get_rank(), dist.get_world_size(), local
+
+
+def barrier_max(t, world):
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([t], dtype=torch.float64, device="cuda")
+    dist.barrier()
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# -------------------------------------------------------------- workloads
+def make_inputs(name, n_rhs):
+    import numpy as np
+    from seeded_inputs import WORKLOADS, workload_links, workload_source
+    w = dict(WORKLOADS[name])
+    links = workload_links(name)
+    src = np.stack([workload_source(name, i) for i in range(n_rhs)])
+    return w, links, src
+
+
+def cpu_oracle_rate(w, links, src0, iters_per_rhs):
+    """Time one oracle BiCG iteration (two operator products + vector updates) on the
+    full field and convert to sources/s with the given iterations per source."""
+    import numpy as np
+    from oracle.wilson import WilsonOperator
+    op = WilsonOperator(links, w["kappa"], w["dims"])
+    b = src0
+    x = np.zeros_like(b)
+    r = b.copy()
+    rh = r.copy()
+    p = r.copy()
+    ph = rh.copy()
+    rho = np.vdot(rh, r)
+    t0 = time.perf_counter()
+    ap = op.apply(p)
+    ahp = op.apply_dag(ph)
+    alpha = rho / np.vdot(ph, ap)
+    x = x + alpha * p
+    r = r - alpha * ap
+    rh = rh - np.conj(alpha) * ahp
+    rho2 = np.vdot(rh, r)
+    beta = rho2 / rho
+    p = r + beta * p
+    ph = rh + np.conj(beta) * ph
+    _ = np.linalg.norm(r)
+    t_iter = time.perf_counter() - t0
+    return 1.0 / (t_iter * iters_per_rhs), t_iter
+
+
+def solver_args(w, precision="mixed", k_max=8):
+    return dict(nev=w["nev"], m=w["m"], n1=w["n1"], tol=1e-10, maxiter=4000, precision=precision,
+                k_max=k_max, n_def_max=min(80, w["n1"] * w["nev"]))
+
+
+def run_job(s, b, x, n1, mode_auto=True):
+    """One step: empty eigenspace, eigBiCG on the first n1 sources, deflated on the rest."""
+    s.reset_eigenspace()
+    x.zero_() if hasattr(x, "zero_") else x.fill(0)
+    _, i1, _ = s.solve(b[:n1], mode="auto", out=x[:n1])
+    _, i2, _ = s.solve(b[n1:], mode="auto", out=x[n1:])
+    return i1 + i2
+
+
+def main_ours(args):
+    import numpy as np
+    import torch
+    from paper_0911_2285_gb300 import Solver
+    from paper_0911_2285_gb300.lqcd import kernel_launches
+
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w, links, src = make_inputs(args.workload, args.n_rhs or w_default(args.workload))
+    n_rhs = src.shape[0]
+    n1 = min(w["n1"], n_rhs)
+    stream = torch.cuda.current_stream(dev)
+    s = Solver(links, w["dims"], w["kappa"], stream=stream.cuda_stream, **solver_args(w))
+    b_dev = torch.from_numpy(src).to(dev)
+    x_dev = torch.zeros_like(b_dev)
+
+    # warm-up (also builds the CUDA graphs)
+    for _ in range(args.warmup):
+        run_job(s, b_dev, x_dev, n1)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timing
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        infos = run_job(s, b_dev, x_dev, n1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    dev_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    dev_ms = barrier_max(dev_ms, world)
+    step_ms = dev_ms / args.steps
+    worst = max(i["true_resid"] for i in infos)
+    if worst > 1e-10:
+        raise SystemExit(f"solution check failed: true residual {worst}")
+    value = n_rhs * world / (step_ms / 1e3)
+    it_eig = float(np.mean([i["iters"] for i in infos[:n1]]))
+    it_def = float(np.mean([i["iters"] for i in infos[n1:]])) if n_rhs > n1 else None
+    mv_per_rhs = float(np.mean([i["matvecs"] for i in infos]))
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        b_host = torch.from_numpy(src).pin_memory()
+        x_host = torch.zeros_like(b_host).pin_memory()
+        run_job(s, b_host, x_host, n1)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            run_job(s, b_host, x_host, n1)
+        torch.cuda.synchronize()
+        e2e_s = barrier_max((time.perf_counter() - t0) / args.steps, world)
+        nbytes = src.nbytes
+        e2e = {"value": n_rhs * world / e2e_s, "unit": "RHS/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+        del b_host, x_host
+
+    # ---- roofline of the operator pair (batched k = 8, FP32) timed live
+    k = min(8, n_rhs)
+    reps = 20
+    op_ms = s.time_kernel(0, k, reps)
+    V = int(np.prod(w["dims"]))
+    alg_bytes = V * (HBM_BYTES_PER_SITE_PAIR["links"] + k * HBM_BYTES_PER_SITE_PAIR["per_rhs"])
+    achieved = alg_bytes / (op_ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    traffic = recorded_traffic(f"dhop_pair_f32_k{k}_{args.workload.replace('^', '').replace('x', 'x')}")
+    upd_ms = s.time_kernel(1, k, reps)
+    dir_ms = s.time_kernel(2, k, reps)
+
+    # ---- plain FP64 single-RHS BiCG on the same GPU (the comparison rate)
+    plain = None
+    if args.plain_rhs > 0:
+        s64 = Solver(links, w["dims"], w["kappa"], stream=stream.cuda_stream,
+                     **solver_args(w, precision="fp64", k_max=1))
+        bp = b_dev[: args.plain_rhs].clone()
+        xp = torch.zeros_like(bp)
+        s64.solve(bp[:1], mode="plain", out=xp[:1])   # warm-up / graph build
+        xp.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, ip, _ = s64.solve(bp, mode="plain", out=xp)
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - t0
+        plain = {"value": args.plain_rhs / tp, "unit": "RHS/s", "precision": "fp64", "k": 1,
+                 "iters_per_rhs": float(np.mean([i["iters"] for i in ip])),
+                 "speedup_of_value": value / world / (args.plain_rhs / tp)}
+        s64.close()
+        del bp, xp
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, t_iter = cpu_oracle_rate(w, links, src[0], (it_eig * n1 + (it_def or 0) * (n_rhs - n1)) / n_rhs)
+        cpu = {"value": rate, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+               "sample": f"1 oracle BiCG iteration (A p, A^+ phat, vector updates; numpy FP64, one thread) on the "
+                         f"full {args.workload} field took {t_iter:.2f} s; scaled by the GPU job's mean "
+                         f"{(it_eig * n1 + (it_def or 0) * (n_rhs - n1)) / n_rhs:.1f} iterations per source"}
+
+    s.close()
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} Wilson-Dirac, random SU(3) links eps={w['eps']}, "
+                               f"kappa={w['kappa']}, {n_rhs} Z2 sources; Incremental eigBiCG (eigBiCG on "
+                               f"{n1} sources, nev={w['nev']} m={w['m']}, then deflated BiCG), batches of 8, "
+                               f"FP32 Krylov + FP64 reliable updates, tol 1e-10",
+                   "dims": list(w["dims"]), "n_rhs": n_rhs, "n1": n1, "nev": w["nev"], "m": w["m"],
+                   "k": 8, "precision": "mixed", "parallelism": f"independent jobs x{world}",
+                   "l2": "inputs larger than L2 (each step streams GBs of fields)"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "iters_per_rhs": {"eigbicg": it_eig, "deflated": it_def, "matvecs_per_rhs": mv_per_rhs},
+        "plain_fp64_bicg": plain,
+        "roofline": {"bound": "hbm", "kernel": "operator pair A p, A^+ phat (FP32, k=8 batch)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": "measured" if peaks else "fallback", "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes, "ms_per_launch": op_ms},
+        "kernel_ms": {"dhop_pair": op_ms, "update": upd_ms, "direction": dir_ms},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def w_default(name):
+    from seeded_inputs import WORKLOADS
+    return WORKLOADS[name]["n_rhs"]
+
+
+def main_reference(args):
+    """The CPU oracle on the same workload: each step is one oracle BiCG iteration on the
+    full field, scaled to sources/s with the FP64 BiCG iteration count of this workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    w, links, src = make_inputs(args.workload, 1)
+    iters = REF_ITERS.get(args.workload, 120)
+    rates, times = [], []
+    for i in range(args.warmup + args.steps):
+        rate, t_iter = cpu_oracle_rate(w, links, src[0], iters)
+        if i >= args.warmup:
+            rates.append(rate)
+            times.append(t_iter)
+    value = float(np.mean(rates))
+    sample = (f"per step 1 oracle BiCG iteration on the full {args.workload} field (numpy FP64, one thread, "
+              f"{np.mean(times):.2f} s), scaled by {iters} BiCG iterations per source")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} Wilson-Dirac, kappa={w['kappa']}", "dims": list(w["dims"])},
+        "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# Plain FP64 BiCG iterations per source to 1e-10 on each workload (Z2 source 0),
+# counted by the library's FP64 BiCG, which runs the oracle's iteration.
+REF_ITERS = {"4^4": 58, "8^4": 113, "16^3x32": 120, "24^3x64": 120}
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

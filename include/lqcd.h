@@ -155,7 +155,9 @@ lqcd_status lqcd_eigspace_get(lqcd_ctx *ctx, double *Ur, double *Ul, double *H);
 
 /* Replace the eigenspace (resume / tests): n pairs of host fields; H is
  * recomputed on the device as U_l^+ A U_r in FP64 and factorised.
- * n = 0 empties it.  LQCD_ERR_ARG if n > n_def_max. */
+ * n = 0 empties it and restarts the LQCD_MODE_AUTO count of eigBiCG sources;
+ * n > 0 counts as a complete eigenspace (AUTO then deflates).
+ * LQCD_ERR_ARG if n > n_def_max. */
 lqcd_status lqcd_eigspace_set(lqcd_ctx *ctx, int n, const double *Ur, const double *Ul);
 
 /* Inspect the eigBiCG window of the most recent eigBiCG solve (batch slot
@@ -176,6 +178,18 @@ lqcd_status lqcd_small_eig(int n, const double *C, double *evals, double *Y, dou
  * Yc, Zc (m x r row-major complex, capacity m*2nev) and lam (r complex). */
 lqcd_status lqcd_restart_coefficients(int m, int nev, const double *H, int *r,
                                       double *Yc, double *Zc, double *lam);
+
+/* Measurement hook (not part of the paper's method): number of kernels this
+ * library has launched in the process so far (graph replays count their nodes). */
+long long lqcd_kernel_launches(void);
+
+/* Measurement hook: average device time (CUDA events on the context's stream)
+ * of one launch of an iteration kernel over batch slots 0..k-1, on whatever the
+ * slot buffers hold, repeated reps times. kernel: 0 = operator pair
+ * A p, A^+ phat (Krylov precision) with the fused sigma reduction; 1 = residual
+ * update; 2 = direction update; 3 = FP64 true residual + reliable-update
+ * replacement. Leaves the slots idle. */
+lqcd_status lqcd_time_kernel(lqcd_ctx *ctx, int kernel, int k, int reps, double *avg_ms);
 
 /* Text for a status code. */
 const char *lqcd_status_str(lqcd_status s);

@@ -666,6 +666,7 @@ cudaError_t launch_small_eig(int n, const double2* A, int lda, int nsel, double2
     cudaError_t e = set_smem((const void*)small_eig_kernel, sm);
     if (e != cudaSuccess) return e;
     small_eig_kernel<<<1, ET, sm, st>>>(n, A, lda, nsel, lam, Y, Z, ldyz, w, info);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -676,6 +677,7 @@ cudaError_t launch_restart_coeffs_single(int m, int nev, const double2* H, int* 
     cudaError_t e = set_smem((const void*)restart_single_kernel, sm);
     if (e != cudaSuccess) return e;
     restart_single_kernel<<<1, ET, sm, st>>>(m, nev, H, r, Yc, Zc, lam, w, info);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -686,6 +688,7 @@ cudaError_t launch_restart_coeffs(SlotState* states, const SlotPtrs* ptrs, int n
     const size_t stride = eig_work_elems();
     size_t sm = EigSmem::bytes(MAX_M);
     restart_slots_kernel<<<nslots, ET, sm, st>>>(states, ptrs, w, stride);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -693,17 +696,20 @@ cudaError_t launch_final_ritz(SlotState* states, const SlotPtrs* ptrs, int slot,
                               double2* lam, int* nout, double2* w, cudaStream_t st) {
     size_t sm = EigSmem::bytes(MAX_M);
     final_ritz_kernel<<<1, ET, sm, st>>>(states, ptrs, slot, Yc, Zc, lam, nout, w);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lu_factor(int n, double2* A, int lda, int* piv, int* info, cudaStream_t st) {
     lu_factor_kernel<<<1, 256, 0, st>>>(n, A, lda, piv, info);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lu_solve(int n, const double2* LU, int lda, const int* piv, int trans, int nrhs, double2* B,
                             int ldb, cudaStream_t st) {
     lu_solve_kernel<<<1, 128, 0, st>>>(n, LU, lda, piv, trans, nrhs, B, ldb);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -712,6 +718,7 @@ cudaError_t launch_small_gemm(int n, int k, int m, const double2* A, int lda, in
     int blocks = (n * m + 255) / 256;
     if (blocks < 1) blocks = 1;
     small_gemm_kernel<<<blocks, 256, 0, st>>>(n, k, m, A, lda, transA, B, ldb, C, ldc);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -610,6 +610,11 @@ __global__ void __launch_bounds__(BL_THREADS) window_gemm_kernel(SlotState* stat
 // ------------------------------------------------------------------ launchers
 static Geom geom_of(const Geom& g) { return g; }
 
+static long long g_launches = 0;
+void count_launches(long long n) { g_launches += n; }
+long long launches_so_far() { return g_launches; }
+void set_launches(long long n) { g_launches = n; }
+
 cudaError_t launch_apply(const Geom& g, const void* links, double kappa, int precision, const ApplyJob* d_jobs,
                          int njobs, int residual, cudaStream_t st) {
     dim3 grid(ds_blocks(g.V), njobs);
@@ -620,6 +625,7 @@ cudaError_t launch_apply(const Geom& g, const void* links, double kappa, int pre
         if (residual) return cudaErrorInvalidValue;
         apply_kernel<float, false><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs);
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -627,12 +633,14 @@ cudaError_t launch_pack(const double* aos, void* dev, int V, int k, int precisio
     int nb = blas_blocks((size_t)V * 12 * k);
     if (precision == 0) pack_kernel<double><<<nb, BL_THREADS, 0, st>>>(reinterpret_cast<const double2*>(aos), dev, V, k);
     else pack_kernel<float><<<nb, BL_THREADS, 0, st>>>(reinterpret_cast<const double2*>(aos), dev, V, k);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t launch_unpack(const void* dev, double* aos, int V, int k, int precision, cudaStream_t st) {
     int nb = blas_blocks((size_t)V * 12 * k);
     if (precision == 0) unpack_kernel<double><<<nb, BL_THREADS, 0, st>>>(dev, reinterpret_cast<double2*>(aos), V, k);
     else unpack_kernel<float><<<nb, BL_THREADS, 0, st>>>(dev, reinterpret_cast<double2*>(aos), V, k);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t launch_convert(const void* src, int sp, void* dst, int dp, size_t n, cudaStream_t st) {
@@ -641,6 +649,7 @@ cudaError_t launch_convert(const void* src, int sp, void* dst, int dp, size_t n,
     else if (sp == 1 && dp == 0) convert_kernel<float, double><<<nb, BL_THREADS, 0, st>>>(src, dst, n);
     else if (sp == 0 && dp == 0) convert_kernel<double, double><<<nb, BL_THREADS, 0, st>>>(src, dst, n);
     else convert_kernel<float, float><<<nb, BL_THREADS, 0, st>>>(src, dst, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -660,6 +669,7 @@ cudaError_t launch_multidot(int a, const void* X, int xp, int b, const void* Y, 
         else if (xp == 1 && yp == 0) multidot_kernel<float, double, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
         else if (xp == 0 && yp == 1) multidot_kernel<double, float, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
         else multidot_kernel<double, double, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
+        count_launches(2);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         double2* Cj = conj_store ? Cm + j0 * ldc : Cm + j0;
@@ -682,6 +692,7 @@ cudaError_t launch_vupdate(int a, const void* X, int xp, const double2* D, int l
         else if (xp == 1 && yp == 0) vupdate_kernel<float, double, float><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
         else if (xp == 0 && yp == 1) vupdate_kernel<double, float, double><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
         else vupdate_kernel<double, double, double><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
+        count_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -692,6 +703,7 @@ cudaError_t launch_scale_fields(int b, void* Y, int yp, const double2* sc, size_
     int nb = blas_blocks(N * b);
     if (yp == 0) scale_fields_kernel<double><<<nb, BL_THREADS, 0, st>>>(b, Y, sc, N);
     else scale_fields_kernel<float><<<nb, BL_THREADS, 0, st>>>(b, Y, sc, N);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -701,6 +713,7 @@ cudaError_t launch_bicg_start(const Geom& g, const void* links64, double kappa, 
     dim3 grid(blas_blocks(N / 2), nslots);
     if (prec == 0) start_kernel<double><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
     else start_kernel<float><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -709,6 +722,7 @@ cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, i
     dim3 grid(ds_blocks(g.V), 2 * nslots);
     if (prec == 0) matvec_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links, kappa, states, ptrs);
     else matvec_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links, kappa, states, ptrs);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -716,6 +730,7 @@ cudaError_t launch_bicg_update(int prec, SlotState* states, const SlotPtrs* ptrs
     dim3 grid(blas_blocks(N / 2), nslots);
     if (prec == 0) update_kernel<double><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
     else update_kernel<float><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -724,16 +739,19 @@ cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int
     dim3 grid(ds_blocks(g.V), nslots);
     if (prec == 0) true_resid_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 0);
     else true_resid_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 0);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 g2(blas_blocks(N / 2), nslots);
     if (prec == 0) replace_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     else replace_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bicg_scalars(SlotState* states, const SlotPtrs* ptrs, int nslots, cudaStream_t s) {
     scalars_kernel<<<nslots, 32, 0, s>>>(states, ptrs);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -742,6 +760,7 @@ cudaError_t launch_bicg_direction(int prec, SlotState* states, const SlotPtrs* p
     dim3 grid(blas_blocks(N / 2), nslots);
     if (prec == 0) direction_kernel<double><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
     else direction_kernel<float><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -750,11 +769,13 @@ cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa,
     dim3 g2(blas_blocks(N / 2), nslots);
     if (prec == 0) fold_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     else fold_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 grid(ds_blocks(g.V), nslots);
     if (prec == 0) true_resid_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 1);
     else true_resid_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 1);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -778,6 +799,7 @@ static cudaError_t window_gemm_dispatch(int rmax_needed, SlotState* states, cons
     } else {
         return cudaErrorInvalidValue;
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 

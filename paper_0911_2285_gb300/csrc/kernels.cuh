@@ -7,6 +7,12 @@
 
 namespace lqcd {
 
+// Process-wide count of kernels launched by this library (graph replays add
+// their node count). Used by the benchmark to report its launch count.
+void count_launches(long long n);
+long long launches_so_far();
+void set_launches(long long n);
+
 constexpr int PARTIAL_STRIDE = 16384;  // double2 per counter kind per slot
 constexpr int MAX_SLOTS = 8;
 constexpr int MAX_M = 64;              // window size limit

@@ -99,6 +99,7 @@ struct lqcd_ctx {
 
     // CUDA graphs of CHECK_EVERY iterations, keyed by (nslots, windowed)
     cudaGraphExec_t graphs[MAX_SLOTS + 1][2] = {};
+    long long graph_nodes[MAX_SLOTS + 1][2] = {};
 
     // last eigBiCG window info (per slot): final Ritz values
     std::vector<std::vector<double2>> last_ritz;
@@ -293,7 +294,10 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     AL(c->dconst, 64 * 16);
 #undef AL
     if ((e = cudaMemset(c->counters, 0, K * CNT_COUNT * sizeof(unsigned))) != cudaSuccess ||
-        (e = cudaMemset(c->small_all, 0, K * c->small_stride * 16)) != cudaSuccess) {
+        (e = cudaMemset(c->small_all, 0, K * c->small_stride * 16)) != cudaSuccess ||
+        (e = cudaMemset(c->win_all, 0, K * 2 * (c->m + 1) * c->kbytes)) != cudaSuccess ||
+        (e = cudaMemset(c->vec_all, 0, K * 6 * c->kbytes)) != cudaSuccess ||
+        (e = cudaMemset(c->x_lo_all, 0, K * c->kbytes)) != cudaSuccess) {
         set_error("cudaMemset", e);
         return fail(LQCD_ERR_CUDA);
     }
@@ -313,6 +317,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     e = cudaMemcpy(tmp, links, (size_t)c->V * 4 * 9 * 16, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         links_kernel<<<1216, 256, 0, c->stream>>>(tmp, c->links64, c->links32, c->V);
+        count_launches(1);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -465,6 +470,7 @@ lqcd_status refactor(lqcd_ctx* c) {
     if (n == 0) return LQCD_OK;
     copy_block_kernel<<<64, 256, 0, c->stream>>>(c->Hdef, ld, c->Hlu, ld, n, n);
     copy_block_kernel<<<64, 256, 0, c->stream>>>(c->Mdef, ld, c->Mlu, ld, n, n);
+    count_launches(2);
     CK(cudaGetLastError());
     CK(launch_lu_factor(n, c->Hlu, ld, c->Hpiv, c->dinfo, c->stream));
     CK(launch_lu_factor(n, c->Mlu, ld, c->Mpiv, c->dinfo + 1, c->stream));
@@ -501,6 +507,7 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, double2* work) {
         CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 1, nn, G2, nn, c->stream));
         negate_kernel<<<1, 256, 0, c->stream>>>(G, n * nn);
         negate_kernel<<<1, 256, 0, c->stream>>>(G2, n * nn);
+        count_launches(2);
         CK(cudaGetLastError());
         CK(launch_vupdate(n, c->Ur, kp, G, nn, nn, Vn, kp, 0, c->N, c->stream));
         CK(launch_vupdate(n, c->Ul, kp, G2, nn, nn, Wn, kp, 0, c->N, c->stream));
@@ -511,6 +518,7 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, double2* work) {
     inv_norm_kernel<<<1, 64, 0, c->stream>>>(NW0, nn, nn, sc + 32, nrm + nn);
     inv_norm_kernel<<<1, 64, 0, c->stream>>>(NV1, nn, nn, sc, nrm + 2 * nn);
     inv_norm_kernel<<<1, 64, 0, c->stream>>>(NW1, nn, nn, sc + nn, nrm + 3 * nn);
+    count_launches(4);
     CK(cudaGetLastError());
     std::vector<double> hn(4 * nn);
     CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * 4 * nn, cudaMemcpyDeviceToHost, c->stream));
@@ -557,16 +565,28 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, double2* work) {
         CK(cudaMemcpyAsync(AW + (size_t)j * c->N, c->staging, c->dbytes, cudaMemcpyDeviceToDevice, c->stream));
     }
     // blocks of H (ld n_def_max): [H, U_l^H AV'; (A^H W')^H U_r, W'^H AV']
-    // and of M: [M, U_l^H V'; W'^H U_r, W'^H V']
+    // and of M: [M, U_l^H V'; W'^H U_r, W'^H V']. With FP32 storage the
+    // projections run in FP32 on FP32 copies of A V', A^H W' (FP64 sums per block).
     double2* Hn = c->Hdef;
     double2* Mn = c->Mdef;
+    const void* AVp = AV;
+    const void* AWp = AW;
+    int ap = 0;
+    if (kp) {
+        char* f32 = reinterpret_cast<char*>(AW + (size_t)kk * c->N);
+        CK(launch_convert(AV, 0, f32, 1, (size_t)kk * c->N, c->stream));
+        CK(launch_convert(AW, 0, f32 + (size_t)kk * c->kbytes, 1, (size_t)kk * c->N, c->stream));
+        AVp = f32;
+        AWp = f32 + (size_t)kk * c->kbytes;
+        ap = 1;
+    }
     if (n > 0) {
-        CK(launch_multidot(n, c->Ul, kp, kk, AV, 0, c->N, Hn + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
-        CK(launch_multidot(n, c->Ur, kp, kk, AW, 0, c->N, Hn + (size_t)n * ld, ld, 1, c->mdscratch, c->mdscratch_elems, c->stream));
+        CK(launch_multidot(n, c->Ul, kp, kk, AVp, ap, c->N, Hn + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+        CK(launch_multidot(n, c->Ur, kp, kk, AWp, ap, c->N, Hn + (size_t)n * ld, ld, 1, c->mdscratch, c->mdscratch_elems, c->stream));
         CK(launch_multidot(n, c->Ul, kp, kk, Vn, kp, c->N, Mn + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
         CK(launch_multidot(n, c->Ur, kp, kk, Wn, kp, c->N, Mn + (size_t)n * ld, ld, 1, c->mdscratch, c->mdscratch_elems, c->stream));
     }
-    CK(launch_multidot(kk, Wn, kp, kk, AV, 0, c->N, Hn + (size_t)n * ld + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_multidot(kk, Wn, kp, kk, AVp, ap, c->N, Hn + (size_t)n * ld + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
     CK(launch_multidot(kk, Wn, kp, kk, Vn, kp, c->N, Mn + (size_t)n * ld + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
     c->n_def = n + kk;
     return refactor(c);
@@ -616,16 +636,22 @@ lqcd_status run_chunk(lqcd_ctx* c, int nslots, int windowed) {
     cudaGraphExec_t& ge = c->graphs[nslots][windowed];
     if (!ge) {
         cudaGraph_t graph = nullptr;
+        const long long before = launches_so_far();   // captured launches are not executions
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         lqcd_status s = enqueue_chunk(c, nslots, windowed);
         cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        set_launches(before);
         if (s != LQCD_OK) { if (graph) cudaGraphDestroy(graph); return s; }
         if (e != cudaSuccess) { set_error("cudaStreamEndCapture", e); return LQCD_ERR_CUDA; }
+        size_t nodes = 0;
+        cudaGraphGetNodes(graph, nullptr, &nodes);
+        c->graph_nodes[nslots][windowed] = (long long)nodes;
         e = cudaGraphInstantiate(&ge, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) { ge = nullptr; set_error("cudaGraphInstantiate", e); return LQCD_ERR_CUDA; }
     }
     CK(cudaGraphLaunch(ge, c->stream));
+    count_launches(c->graph_nodes[nslots][windowed]);
     return LQCD_OK;
 }
 
@@ -692,9 +718,9 @@ lqcd_status grow_from_windows(lqcd_ctx* c, int k) {
         CK(launch_vupdate(vs, P.W, c->kprec, Zc, nsel, take, c->krylov(c->Ul, c->n_def), c->kprec, 1, c->N, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         c->last_ritz[s] = hl;
-        // FP64 work fields for A V', A^H W': this slot's window (>= 2*take FP64 fields)
+        // work fields for A V', A^H W' (FP64, plus their FP32 copies in MIXED): this
+        // slot's window, which holds 2(m+1) > 4 nev Krylov fields
         double2* work = reinterpret_cast<double2*>(P.V);
-        if ((size_t)2 * (c->m + 1) * c->kbytes < (size_t)2 * take * c->dbytes) work = c->rt_all;  // tiny windows
         lqcd_status r = grow_space(c, take, work);
         if (r != LQCD_OK) return r;
         c->eig_rhs_done += 1;
@@ -794,6 +820,7 @@ extern "C" lqcd_status lqcd_eigspace_set(lqcd_ctx* c, int n, const double* Ur, c
     if (!c || n < 0 || n > c->n_def_max) return LQCD_ERR_ARG;
     if (n > 0 && (!Ur || !Ul)) return LQCD_ERR_ARG;
     c->n_def = 0;
+    c->eig_rhs_done = 0;
     if (n == 0) return LQCD_OK;
     lqcd_status s = upload(c, Ur, n, c->Ur, c->kprec, 0);
     if (s != LQCD_OK) return s;
@@ -817,6 +844,7 @@ extern "C" lqcd_status lqcd_eigspace_set(lqcd_ctx* c, int n, const double* Ur, c
                            c->mdscratch_elems, c->stream));
     }
     c->n_def = n;
+    c->eig_rhs_done = c->p.n1;   // a loaded eigenspace counts as complete for LQCD_MODE_AUTO
     s = refactor(c);
     if (s != LQCD_OK) return s;
     CK(cudaStreamSynchronize(c->stream));
@@ -837,6 +865,7 @@ extern "C" lqcd_status lqcd_eigs(lqcd_ctx* c, int* n_inout, double* evals, doubl
     double2* Z = Y + (size_t)n * n;
     double2* lam = Z + (size_t)n * n;
     copy_block_kernel<<<64, 256, 0, c->stream>>>(c->Hdef, ld, G, n, n, n);
+    count_launches(1);
     CK(cudaGetLastError());
     CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 0, n, G, n, c->stream));
     CK(launch_small_eig(n, G, n, n, lam, Y, Z, n, c->dinfo + 16, c->eigwork, c->stream));
@@ -971,4 +1000,53 @@ extern "C" lqcd_status lqcd_restart_coefficients(int m, int nev, const double* H
     }
     cudaFree(dH); cudaFree(dY); cudaFree(dZ); cudaFree(dl); cudaFree(dw); cudaFree(di);
     return ret;
+}
+
+// ============================================================ measurement
+extern "C" long long lqcd_kernel_launches(void) { return launches_so_far(); }
+
+extern "C" lqcd_status lqcd_time_kernel(lqcd_ctx* c, int kernel, int k, int reps, double* avg_ms) {
+    if (!c || !avg_ms || k < 1 || k > c->kmax || reps < 1) return LQCD_ERR_ARG;
+    if (kernel < 0 || kernel > 3) return LQCD_ERR_ARG;
+    // Slots 0..k-1 iterate with fixed scalars on whatever their buffers hold.
+    std::vector<SlotState> tmpl(c->kmax);
+    for (int s = 0; s < c->kmax; ++s) {
+        SlotState& st = tmpl[s];
+        memset(&st, 0, sizeof(SlotState));
+        st.status = s < k ? ST_RUNNING : ST_IDLE;
+        st.live = s < k;
+        st.need_ru = 1;
+        st.tol = 0.0;
+        st.maxiter = 1 << 30;
+        st.rho = make_double2(1.0, 0.0);
+        st.rnorm = 1.0; st.bnorm = 1.0; st.rmax = 1.0;
+        st.alpha = make_double2(0.1, 0.0);
+        st.beta = make_double2(0.1, 0.0);
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
+    double total = 0.0;
+    for (int r = 0; r < reps; ++r) {
+        CK(cudaMemcpyAsync(c->d_state, tmpl.data(), sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaEventRecord(e0, c->stream));
+        if (kernel == 0) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->stream));
+        else if (kernel == 1) CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
+        else if (kernel == 2) CK(launch_bicg_direction(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
+        else CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        total += ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // leave the slots idle
+    for (int s = 0; s < c->kmax; ++s) { tmpl[s].status = ST_IDLE; tmpl[s].live = 0; }
+    CK(cudaMemcpyAsync(c->d_state, tmpl.data(), sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *avg_ms = total / reps;
+    return LQCD_OK;
 }

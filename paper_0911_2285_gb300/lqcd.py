@@ -95,6 +95,9 @@ def lib():
         L.lqcd_status_str.restype = C.c_char_p
         L.lqcd_last_error.restype = C.c_char_p
         L.lqcd_destroy.argtypes = [vp]
+        L.lqcd_kernel_launches.restype = C.c_longlong
+        L.lqcd_time_kernel.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
+        L.lqcd_time_kernel.restype = C.c_int
         for name in ("lqcd_eigbicg_init", "lqcd_solve", "lqcd_deflate", "lqcd_eigs", "lqcd_apply",
                      "lqcd_eigspace_get", "lqcd_eigspace_set", "lqcd_last_window", "lqcd_small_eig",
                      "lqcd_restart_coefficients"):
@@ -186,11 +189,17 @@ class Solver:
         self.close()
 
     # ---------------------------------------------------------------- calls
-    def solve(self, b, x0=None, mode="auto", raise_on_fail=True):
-        """Solve ``A x = b`` for a batch; returns ``(x, infos, status)``."""
+    def solve(self, b, x0=None, mode="auto", raise_on_fail=True, out=None):
+        """Solve ``A x = b`` for a batch; returns ``(x, infos, status)``.
+
+        ``out`` (optional) receives the solutions in place and must already hold
+        the initial guesses (``x0`` is then ignored).
+        """
         b = _as_batch(b, self.n)
         k = b.shape[0]
-        if x0 is None:
+        if out is not None:
+            x = _as_batch(out, self.n)
+        elif x0 is None:
             x = _zeros_like(b)
         else:
             x = _as_batch(x0, self.n)
@@ -237,6 +246,16 @@ class Solver:
         _check(st, "lqcd_eigs")
         k = cnt.value
         return ev[:k], res[:k], (ur[:k] if vectors else None), (ul[:k] if vectors else None)
+
+    def reset_eigenspace(self):
+        """Empty the eigenspace (AUTO mode starts over with eigBiCG)."""
+        _check(lib().lqcd_eigspace_set(self._h, 0, None, None), "lqcd_eigspace_set")
+
+    def time_kernel(self, kernel, k, reps=10):
+        """Average device ms of one launch of an iteration kernel (see lqcd_time_kernel)."""
+        ms = C.c_double()
+        _check(lib().lqcd_time_kernel(self._h, int(kernel), int(k), int(reps), C.byref(ms)), "lqcd_time_kernel")
+        return ms.value
 
     def eigspace_size(self):
         return lib().lqcd_eigspace_size(self._h)
@@ -290,6 +309,11 @@ def _zeros_like(a):
     except ImportError:  # pragma: no cover
         pass
     return np.zeros_like(a)
+
+
+def kernel_launches():
+    """Kernels launched by the library in this process so far."""
+    return int(lib().lqcd_kernel_launches())
 
 
 def small_eig(c):
