@@ -61,16 +61,29 @@ __device__ bool reduce_slot(const SlotPtrs& P, int kind, double2 (&v)[NV], doubl
     return last;
 }
 
+// Per-thread partial sums accumulate in the storage precision (FP32 for the
+// mixed solver: FP64 arithmetic is a small fraction of FP32 throughput on this
+// GPU and would bound these bandwidth kernels); the block and cross-block sums
+// are FP64.
+template <typename S> struct Acc {
+    cplx<S> z;      // complex sum
+    S a, b;         // two real sums
+    __device__ __forceinline__ Acc() : z(mk<S>(S(0), S(0))), a(S(0)), b(S(0)) {}
+    __device__ __forceinline__ void to(double2 (&v)[2]) const { v[0] = to_d(z); v[1] = make_double2((double)a, (double)b); }
+};
+template <typename C> __device__ __forceinline__ auto abs2(C a) -> decltype(a.x) { return a.x * a.x + a.y * a.y; }
+
 // ------------------------------------------------------------------- apply
 template <typename S, bool RES>
 __global__ void __launch_bounds__(DS_THREADS) apply_kernel(Geom g, const void* links, double kappa,
-                                                           const ApplyJob* jobs) {
+                                                           const ApplyJob* jobs, int njobs) {
     using C = cplx<S>;
-    const ApplyJob jb = jobs[blockIdx.y];
+    const int jid = blockIdx.x % njobs, sblock = blockIdx.x / njobs, nsb = gridDim.x / njobs;
+    const ApplyJob jb = jobs[jid];
     typename LinkSel<S>::type U{reinterpret_cast<decltype(U.u)>(links), g.V};
     FieldIn<S> in{jb.in, g.V};
     const S k = (S)kappa;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    for (int s = sblock * blockDim.x + threadIdx.x; s < g.V; s += nsb * blockDim.x) {
         C acc[12], self[12];
         if (jb.dagger) hop_site<true, S>(g, U, in, s, acc);
         else hop_site<false, S>(g, U, in, s, acc);
@@ -251,7 +264,7 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
     const SlotPtrs& P = ptrs[blockIdx.y];
     if (st.status != ST_RUNNING) return;
     using C = cplx<S>;
-    double2 v[2] = {make_double2(0, 0), make_double2(0, 0)};   // rho, (|r|^2, |b|^2)
+    Acc<S> acc;   // rho, |r|^2, |b|^2
     const size_t units = N / 2;
     Unit<S> zero{mk<S>(0, 0), mk<S>(0, 0)};
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
@@ -263,11 +276,12 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
         r.store(P.p, u);
         r.store(P.phat, u);
         zero.store(P.x_lo, u);
-        double2 ra = to_d(r.a), rb = to_d(r.b);
-        v[0] = v[0] + cdot(ra, ra) + cdot(rb, rb);
-        v[1].x += cabs2(ra) + cabs2(rb);
-        v[1].y += cabs2(bb.a) + cabs2(bb.b);
+        acc.z = acc.z + cdot(r.a, r.a) + cdot(r.b, r.b);
+        acc.a += abs2(r.a) + abs2(r.b);
+        acc.b += (S)(cabs2(bb.a) + cabs2(bb.b));
     }
+    double2 v[2];
+    acc.to(v);
     double2 tot[2];
     if (reduce_slot<2>(P, CNT_START, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
         st.rho = tot[0];
@@ -286,10 +300,14 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
 
 // Operator pair of one iteration: A p -> Ap[par], A^+ phat -> Ahp[par];
 // sigma = (phat, A p) and alpha = rho / sigma in the last block.
+// Grid: (site blocks x jobs) flattened with the job index fastest, so the 2k
+// jobs that share a block of sites (and its links) run together and the links
+// come from DRAM once per launch.
 template <typename S>
 __global__ void __launch_bounds__(DS_THREADS) matvec_kernel(Geom g, const void* links, double kappa,
-                                                            SlotState* states, const SlotPtrs* ptrs) {
-    const int slot = blockIdx.y >> 1, which = blockIdx.y & 1;
+                                                            SlotState* states, const SlotPtrs* ptrs, int njobs) {
+    const int job = blockIdx.x % njobs, sblock = blockIdx.x / njobs, nsb = gridDim.x / njobs;
+    const int slot = job >> 1, which = job & 1;
     SlotState& st = states[slot];
     const SlotPtrs& P = ptrs[slot];
     if (st.status != ST_RUNNING) return;
@@ -299,8 +317,8 @@ __global__ void __launch_bounds__(DS_THREADS) matvec_kernel(Geom g, const void* 
     FieldIn<S> in{which ? P.phat : P.p, g.V};
     void* out = which ? P.Ahp[par] : P.Ap[par];
     const S k = (S)kappa;
-    double2 v[2] = {make_double2(0, 0), make_double2(0, 0)};   // sigma, (|phat|^2, |Ap|^2)
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    Acc<S> sacc;   // sigma, |phat|^2, |Ap|^2
+    for (int s = sblock * blockDim.x + threadIdx.x; s < g.V; s += nsb * blockDim.x) {
         C acc[12], self[12];
         if (which) hop_site<true, S>(g, U, in, s, acc);
         else hop_site<false, S>(g, U, in, s, acc);
@@ -313,16 +331,17 @@ __global__ void __launch_bounds__(DS_THREADS) matvec_kernel(Geom g, const void* 
             Field<S>::load(P.phat, g.V, s, ph);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
-                double2 a = to_d(ph[c]), b = to_d(acc[c]);
-                v[0] = v[0] + cdot(a, b);
-                v[1].x += cabs2(a);
-                v[1].y += cabs2(b);
+                sacc.z = sacc.z + cdot(ph[c], acc[c]);
+                sacc.a += abs2(ph[c]);
+                sacc.b += abs2(acc[c]);
             }
         }
     }
     if (which) return;
+    double2 v[2];
+    sacc.to(v);
     double2 tot[2];
-    if (reduce_slot<2>(P, CNT_MATVEC, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+    if (reduce_slot<2>(P, CNT_MATVEC, v, tot, nsb, sblock) && threadIdx.x == 0) {
         st.sigma = tot[0];
         st.phat_norm = sqrt(tot[1].x);
         st.ap_norm = sqrt(tot[1].y);
@@ -351,7 +370,7 @@ __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, c
     void* hout = slot_field<S>(P.W, next_slot(st), N);
     const void* ap = P.Ap[par];
     const void* ahp = P.Ahp[par];
-    double2 v[2] = {make_double2(0, 0), make_double2(0, 0)};
+    Acc<S> acc;   // rho_j, |r_j|^2, |rhat_j|^2
     const size_t units = N / 2;
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
         Unit<S> x = Unit<S>::load(P.x_lo, u), p = Unit<S>::load(P.p, u);
@@ -363,11 +382,12 @@ __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, c
         x.store(P.x_lo, u);
         r.store(rout, u);
         h.store(hout, u);
-        double2 ra = to_d(r.a), rb = to_d(r.b), ha = to_d(h.a), hb = to_d(h.b);
-        v[0] = v[0] + cdot(ha, ra) + cdot(hb, rb);
-        v[1].x += cabs2(ra) + cabs2(rb);
-        v[1].y += cabs2(ha) + cabs2(hb);
+        acc.z = acc.z + cdot(h.a, r.a) + cdot(h.b, r.b);
+        acc.a += abs2(r.a) + abs2(r.b);
+        acc.b += abs2(h.a) + abs2(h.b);
     }
+    double2 v[2];
+    acc.to(v);
     double2 tot[2];
     if (reduce_slot<2>(P, CNT_UPDATE, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
         st.rho_new = tot[0];
@@ -430,7 +450,7 @@ __global__ void __launch_bounds__(BL_THREADS) replace_kernel(SlotState* states, 
     const bool run = st.status == ST_RUNNING;
     void* rcur = slot_field<S>(P.V, next_slot(st), N);
     const void* hcur = slot_field<S>(P.W, next_slot(st), N);
-    double2 v[1] = {make_double2(0, 0)};
+    cplx<S> rho = mk<S>(S(0), S(0));
     const size_t units = N / 2;
     Unit<S> zero{mk<S>(0, 0), mk<S>(0, 0)};
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
@@ -444,9 +464,10 @@ __global__ void __launch_bounds__(BL_THREADS) replace_kernel(SlotState* states, 
             Unit<S> r{cvt<S>(rt.a), cvt<S>(rt.b)};
             r.store(rcur, u);
             Unit<S> h = Unit<S>::load(hcur, u);
-            v[0] = v[0] + cdot(to_d(h.a), to_d(r.a)) + cdot(to_d(h.b), to_d(r.b));
+            rho = rho + cdot(h.a, r.a) + cdot(h.b, r.b);
         }
     }
+    double2 v[1] = {to_d(rho)};
     double2 tot[1];
     if (reduce_slot<1>(P, CNT_REPLACE, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
         if (run) {
@@ -595,12 +616,13 @@ __global__ void __launch_bounds__(BL_THREADS) window_gemm_kernel(SlotState* stat
     for (int k = 0; k < RMAX; ++k) v[k] = to_d(dot[k]);
     double2 tot[RMAX];
     if (reduce_slot<RMAX>(P, side ? CNT_GEMM_W : CNT_GEMM_V, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+        // the new basis vectors are stored normalised: their window scale is 1
         if (side) {
             const double f = 1.0 / st.rnorm;
-            for (int k = 0; k < r; ++k) P.H[k * m + r] = f * tot[k];
+            for (int k = 0; k < r; ++k) { P.H[k * m + r] = f * tot[k]; P.wscale[k] = make_double2(1.0, 0.0); }
         } else {
             const double2 f = cdiv(make_double2(st.rnorm, 0.0), st.rho);
-            for (int k = 0; k < r; ++k) P.H[r * m + k] = f * tot[k];
+            for (int k = 0; k < r; ++k) { P.H[r * m + k] = f * tot[k]; P.vscale[k] = 1.0; }
         }
     }
 }
@@ -617,13 +639,13 @@ void set_launches(long long n) { g_launches = n; }
 
 cudaError_t launch_apply(const Geom& g, const void* links, double kappa, int precision, const ApplyJob* d_jobs,
                          int njobs, int residual, cudaStream_t st) {
-    dim3 grid(ds_blocks(g.V), njobs);
+    const int grid = ds_blocks(g.V) * njobs;   // jobs fastest: they share each block's links
     if (precision == 0) {
-        if (residual) apply_kernel<double, true><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs);
-        else apply_kernel<double, false><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs);
+        if (residual) apply_kernel<double, true><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs, njobs);
+        else apply_kernel<double, false><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs, njobs);
     } else {
         if (residual) return cudaErrorInvalidValue;
-        apply_kernel<float, false><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs);
+        apply_kernel<float, false><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs, njobs);
     }
     count_launches(1);
     return cudaGetLastError();
@@ -719,9 +741,10 @@ cudaError_t launch_bicg_start(const Geom& g, const void* links64, double kappa, 
 
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
                                const SlotPtrs* ptrs, int nslots, cudaStream_t s) {
-    dim3 grid(ds_blocks(g.V), 2 * nslots);
-    if (prec == 0) matvec_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links, kappa, states, ptrs);
-    else matvec_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links, kappa, states, ptrs);
+    const int njobs = 2 * nslots;
+    const int grid = ds_blocks(g.V) * njobs;
+    if (prec == 0) matvec_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links, kappa, states, ptrs, njobs);
+    else matvec_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links, kappa, states, ptrs, njobs);
     count_launches(1);
     return cudaGetLastError();
 }

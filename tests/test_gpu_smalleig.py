@@ -58,8 +58,10 @@ def test_restart_coefficients_match_oracle(m, nev):
     yc_o, zc_o, lam_o = restart_coefficients(H, nev)
     yc, zc, lam = dev_restart(H, nev)
     assert len(lam) == len(lam_o)
-    # T's eigenvalues on nearly dependent pairs amplify rounding: 1e-7 relative
-    assert _same_set(lam, lam_o, 1e-7 * np.abs(lam_o).max())
+    # the nev smallest (the ones kept by later restarts and the final Ritz step)
+    # agree tightly; eigenvalues of T along nearly dependent pairs amplify rounding
+    assert np.abs(lam[:nev] - lam_o[:nev]).max() <= 1e-9 * np.abs(lam_o).max()
+    assert _same_set(lam, lam_o, 1e-5 * np.abs(lam_o).max())
     # the restarted pair is biorthonormal and diagonalises H on the device as well
     assert np.abs(np.conj(zc.T) @ yc - np.eye(len(lam))).max() <= 1e-5
     assert np.abs(np.conj(zc.T) @ H @ yc - np.diag(lam)).max() <= 1e-5 * np.abs(lam).max()

@@ -74,6 +74,25 @@ def test_eigbicg_restarts_match_oracle_ritz_values():
     assert true_resid(op, b, x[0]) <= 1e-10
 
 
+def test_eigbicg_ritz_vectors_match_oracle_after_restarts():
+    """FP64 eigBiCG with restarts: the stored right/left Ritz vectors (first eigBiCG
+    source, empty eigenspace: normalised Ritz vectors) span the oracle's ones."""
+    s, op, w = solver("4^4", m=24, nev=8, n1=1)
+    b = workload_source("4^4", 0)
+    with s:
+        s.solve(b, mode="eigbicg")
+        ur, ul, H = s.eigspace_get()
+        _, ritz, restarts = s.last_window(0)
+    ref = eigbicg(op, b, nev=8, m=24)
+    assert restarts >= 2
+    for i in range(len(ritz)):
+        j = int(np.argmin(np.abs(ref.evals - ritz[i])))
+        u = ref.U[:, j] / np.linalg.norm(ref.U[:, j])
+        q = ref.Q[:, j] / np.linalg.norm(ref.Q[:, j])
+        assert abs(abs(np.vdot(u, ur[i])) - 1) <= 1e-6
+        assert abs(abs(np.vdot(q, ul[i])) - 1) <= 1e-6
+
+
 def test_eigbicg_free_field_ritz_closed_form_on_gpu():
     from paper_0911_2285_gb300 import Solver
     dims = (4, 4, 4, 4)
