@@ -85,6 +85,25 @@ struct Geom {
     }
 };
 
+// The eight neighbour sites of s (periodic), from one coordinate decomposition.
+struct Nbr {
+    int f[4], b[4];
+    __device__ __forceinline__ Nbr(const Geom& g, int s) {
+        int r = s;
+        int c[4];
+        c[0] = r % g.L[0]; r /= g.L[0];
+        c[1] = r % g.L[1]; r /= g.L[1];
+        c[2] = r % g.L[2];
+        c[3] = r / g.L[2];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const int st = g.stride[mu], wrap = (g.L[mu] - 1) * st;
+            f[mu] = c[mu] == g.L[mu] - 1 ? s - wrap : s + st;
+            b[mu] = c[mu] == 0 ? s + wrap : s - st;
+        }
+    }
+};
+
 // ------------------------------------------------------------ field access
 // Storage type S (float or double); values returned in arithmetic type T.
 template <typename S> struct Field;

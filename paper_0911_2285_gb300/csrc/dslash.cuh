@@ -115,13 +115,13 @@ template <typename S> struct SumIn {
 };
 
 template <int MU, bool DAG, typename T, class LK, class IN>
-__device__ __forceinline__ void hop_dir(const Geom& g, const LK& U, const IN& in, int s,
+__device__ __forceinline__ void hop_dir(const Nbr& nb, const LK& U, const IN& in, int s,
                                         cplx<T> (&acc)[12]) {
     using C = cplx<T>;
     constexpr int SF = DAG ? +1 : -1;   // forward projector sign
     C psi[12], h[2][3], uh[2][3], u[3][3];
     {
-        int sf = g.fwd(s, MU);
+        int sf = nb.f[MU];
         in.load(sf, psi);
         project<MU, SF>(psi, h);
         U.load(MU, s, u);
@@ -129,7 +129,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const LK& U, const IN& in
         reconstruct<MU, SF>(uh, acc);
     }
     {
-        int sb = g.bwd(s, MU);
+        int sb = nb.b[MU];
         in.load(sb, psi);
         project<MU, -SF>(psi, h);
         U.load(MU, sb, u);
@@ -142,12 +142,52 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const LK& U, const IN& in
 template <bool DAG, typename T, class LK, class IN>
 __device__ __forceinline__ void hop_site(const Geom& g, const LK& U, const IN& in, int s,
                                          cplx<T> (&acc)[12]) {
+    const Nbr nb(g, s);
 #pragma unroll
     for (int c = 0; c < 12; ++c) acc[c] = mk<T>(T(0), T(0));
-    hop_dir<0, DAG, T>(g, U, in, s, acc);
-    hop_dir<1, DAG, T>(g, U, in, s, acc);
-    hop_dir<2, DAG, T>(g, U, in, s, acc);
-    hop_dir<3, DAG, T>(g, U, in, s, acc);
+    hop_dir<0, DAG, T>(nb, U, in, s, acc);
+    hop_dir<1, DAG, T>(nb, U, in, s, acc);
+    hop_dir<2, DAG, T>(nb, U, in, s, acc);
+    hop_dir<3, DAG, T>(nb, U, in, s, acc);
+}
+
+// Both operators of a BiCG pair at one site, sharing every link load:
+// a = D_hop p (projectors 1 -+ gamma), b = D_hop^+ phat (projectors 1 +- gamma).
+template <int MU, typename T, class LK, class IN>
+__device__ __forceinline__ void hop_dir_pair(const Nbr& nb, const LK& U, const IN& inp, const IN& inh, int s,
+                                             cplx<T> (&a)[12], cplx<T> (&b)[12]) {
+    using C = cplx<T>;
+    C psi[12], h[2][3], uh[2][3], u[3][3];
+    U.load(MU, s, u);
+    inp.load(nb.f[MU], psi);
+    project<MU, -1>(psi, h);
+    su3_mul(u, h, uh);
+    reconstruct<MU, -1>(uh, a);
+    inh.load(nb.f[MU], psi);
+    project<MU, +1>(psi, h);
+    su3_mul(u, h, uh);
+    reconstruct<MU, +1>(uh, b);
+    U.load(MU, nb.b[MU], u);
+    inp.load(nb.b[MU], psi);
+    project<MU, +1>(psi, h);
+    su3_dag_mul(u, h, uh);
+    reconstruct<MU, +1>(uh, a);
+    inh.load(nb.b[MU], psi);
+    project<MU, -1>(psi, h);
+    su3_dag_mul(u, h, uh);
+    reconstruct<MU, -1>(uh, b);
+}
+
+template <typename T, class LK, class IN>
+__device__ __forceinline__ void hop_site_pair(const Geom& g, const LK& U, const IN& inp, const IN& inh, int s,
+                                              cplx<T> (&a)[12], cplx<T> (&b)[12]) {
+    const Nbr nb(g, s);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) { a[c] = mk<T>(T(0), T(0)); b[c] = a[c]; }
+    hop_dir_pair<0, T>(nb, U, inp, inh, s, a, b);
+    hop_dir_pair<1, T>(nb, U, inp, inh, s, a, b);
+    hop_dir_pair<2, T>(nb, U, inp, inh, s, a, b);
+    hop_dir_pair<3, T>(nb, U, inp, inh, s, a, b);
 }
 
 }  // namespace lqcd

@@ -300,44 +300,69 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
 
 // Operator pair of one iteration: A p -> Ap[par], A^+ phat -> Ahp[par];
 // sigma = (phat, A p) and alpha = rho / sigma in the last block.
-// Grid: (site blocks x jobs) flattened with the job index fastest, so the 2k
-// jobs that share a block of sites (and its links) run together and the links
-// come from DRAM once per launch.
-template <typename S>
-__global__ void __launch_bounds__(DS_THREADS) matvec_kernel(Geom g, const void* links, double kappa,
-                                                            SlotState* states, const SlotPtrs* ptrs, int njobs) {
+// Grid: (site blocks x jobs) flattened with the job index fastest, so the jobs
+// that share a block of sites (and its links) run together and the links come
+// from DRAM once per launch. Variants (picked by the autotuner):
+//   PAIR = false: one thread per (site, operator) job, 2 jobs per slot;
+//   PAIR = true : one thread per (site, slot) computes both operators and
+//                 shares each link load between them.
+template <typename S, int THREADS, int MINB, bool PAIR>
+__global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const void* links, double kappa,
+                                                               SlotState* states, const SlotPtrs* ptrs,
+                                                               int njobs) {
     const int job = blockIdx.x % njobs, sblock = blockIdx.x / njobs, nsb = gridDim.x / njobs;
-    const int slot = job >> 1, which = job & 1;
+    const int slot = PAIR ? job : job >> 1, which = PAIR ? 0 : job & 1;
     SlotState& st = states[slot];
     const SlotPtrs& P = ptrs[slot];
     if (st.status != ST_RUNNING) return;
     using C = cplx<S>;
     const int par = st.iter & 1;
     typename LinkSel<S>::type U{reinterpret_cast<decltype(U.u)>(links), g.V};
-    FieldIn<S> in{which ? P.phat : P.p, g.V};
-    void* out = which ? P.Ahp[par] : P.Ap[par];
     const S k = (S)kappa;
     Acc<S> sacc;   // sigma, |phat|^2, |Ap|^2
-    for (int s = sblock * blockDim.x + threadIdx.x; s < g.V; s += nsb * blockDim.x) {
-        C acc[12], self[12];
-        if (which) hop_site<true, S>(g, U, in, s, acc);
-        else hop_site<false, S>(g, U, in, s, acc);
-        in.load(s, self);
+    if (PAIR) {
+        FieldIn<S> inp{P.p, g.V}, inh{P.phat, g.V};
+        for (int s = sblock * THREADS + threadIdx.x; s < g.V; s += nsb * THREADS) {
+            C a[12], b[12], self[12];
+            hop_site_pair<S>(g, U, inp, inh, s, a, b);
+            inp.load(s, self);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) acc[c] = self[c] - k * acc[c];
-        Field<S>::store(out, g.V, s, acc);
-        if (!which) {
-            C ph[12];
-            Field<S>::load(P.phat, g.V, s, ph);
+            for (int c = 0; c < 12; ++c) a[c] = self[c] - k * a[c];
+            Field<S>::store(P.Ap[par], g.V, s, a);
+            inh.load(s, self);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
-                sacc.z = sacc.z + cdot(ph[c], acc[c]);
-                sacc.a += abs2(ph[c]);
-                sacc.b += abs2(acc[c]);
+                b[c] = self[c] - k * b[c];
+                sacc.z = sacc.z + cdot(self[c], a[c]);
+                sacc.a += abs2(self[c]);
+                sacc.b += abs2(a[c]);
+            }
+            Field<S>::store(P.Ahp[par], g.V, s, b);
+        }
+    } else {
+        FieldIn<S> in{which ? P.phat : P.p, g.V};
+        void* out = which ? P.Ahp[par] : P.Ap[par];
+        for (int s = sblock * THREADS + threadIdx.x; s < g.V; s += nsb * THREADS) {
+            C acc[12], self[12];
+            if (which) hop_site<true, S>(g, U, in, s, acc);
+            else hop_site<false, S>(g, U, in, s, acc);
+            in.load(s, self);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[c] = self[c] - k * acc[c];
+            Field<S>::store(out, g.V, s, acc);
+            if (!which) {
+                C ph[12];
+                Field<S>::load(P.phat, g.V, s, ph);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    sacc.z = sacc.z + cdot(ph[c], acc[c]);
+                    sacc.a += abs2(ph[c]);
+                    sacc.b += abs2(acc[c]);
+                }
             }
         }
+        if (which) return;
     }
-    if (which) return;
     double2 v[2];
     sacc.to(v);
     double2 tot[2];
@@ -739,12 +764,30 @@ cudaError_t launch_bicg_start(const Geom& g, const void* links64, double kappa, 
     return cudaGetLastError();
 }
 
+template <typename S, int THREADS, int MINB, bool PAIR>
+static void matvec_launch(const Geom& g, const void* links, double kappa, SlotState* states, const SlotPtrs* ptrs,
+                          int nslots, cudaStream_t s) {
+    const int njobs = PAIR ? nslots : 2 * nslots;
+    int nb = div_up((size_t)g.V, THREADS);
+    if (nb > PARTIAL_STRIDE / 2) nb = PARTIAL_STRIDE / 2;
+    matvec_kernel<S, THREADS, MINB, PAIR><<<nb * njobs, THREADS, 0, s>>>(g, links, kappa, states, ptrs, njobs);
+}
+
+int matvec_variants() { return 5; }
+
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
-                               const SlotPtrs* ptrs, int nslots, cudaStream_t s) {
-    const int njobs = 2 * nslots;
-    const int grid = ds_blocks(g.V) * njobs;
-    if (prec == 0) matvec_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links, kappa, states, ptrs, njobs);
-    else matvec_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links, kappa, states, ptrs, njobs);
+                               const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant) {
+    if (prec == 0) {
+        matvec_launch<double, 128, 1, false>(g, links, kappa, states, ptrs, nslots, s);
+    } else {
+        switch (variant) {
+            case 1: matvec_launch<float, 128, 6, false>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 2: matvec_launch<float, 256, 3, false>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 3: matvec_launch<float, 128, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 4: matvec_launch<float, 128, 4, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            default: matvec_launch<float, 128, 1, false>(g, links, kappa, states, ptrs, nslots, s); break;
+        }
+    }
     count_launches(1);
     return cudaGetLastError();
 }

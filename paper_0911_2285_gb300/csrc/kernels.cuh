@@ -50,8 +50,10 @@ cudaError_t launch_scale_fields(int b, void* Y, int yprec, const double2* sc, si
 // BiCG iteration kernels over nslots slots (see kernels.cu for the contract).
 cudaError_t launch_bicg_start(const Geom& g, const void* links, double kappa, int prec,
                               SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+// variant: operator-kernel shape chosen by the autotuner (0 .. matvec_variants()-1)
+int matvec_variants();
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec,
-                               SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s);
+                               SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant);
 cudaError_t launch_bicg_update(int prec, SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
 cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int prec,
                            SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);

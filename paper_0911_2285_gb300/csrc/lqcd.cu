@@ -97,6 +97,9 @@ struct lqcd_ctx {
     int* dinfo = nullptr;
     double2* dconst = nullptr;      // constants
 
+    int dslash_variant = 0;         // operator-kernel shape (autotuned at init)
+    std::vector<double> tune_ms;    // autotuner timings per variant
+
     // CUDA graphs of CHECK_EVERY iterations, keyed by (nslots, windowed)
     cudaGraphExec_t graphs[MAX_SLOTS + 1][2] = {};
     long long graph_nodes[MAX_SLOTS + 1][2] = {};
@@ -207,6 +210,8 @@ __global__ void inv_norm_kernel(const double2* G, int ld, int n, double2* sc, do
 
 }  // namespace
 
+static lqcd_status autotune(lqcd_ctx* c);
+
 // ============================================================== lifecycle
 extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* params, const double* links,
                                          void* cuda_stream) {
@@ -290,7 +295,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     AL(c->Hpiv, (size_t)(c->n_def_max + 1) * sizeof(int));
     AL(c->Mpiv, (size_t)(c->n_def_max + 1) * sizeof(int));
     AL(c->dsmall, (size_t)(MAX_SMALL * MAX_SMALL * 6 + 4096) * 16);
-    AL(c->dinfo, 64 * sizeof(int));
+    AL(c->dinfo, (64 + MAX_SMALL) * sizeof(int));
     AL(c->dconst, 64 * 16);
 #undef AL
     if ((e = cudaMemset(c->counters, 0, K * CNT_COUNT * sizeof(unsigned))) != cudaSuccess ||
@@ -327,6 +332,8 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     c->last_vs.assign(c->kmax, 0);
     c->last_restarts.assign(c->kmax, 0);
     if ((e = prepare_eig_kernels()) != cudaSuccess) { set_error("prepare_eig_kernels", e); return fail(LQCD_ERR_CUDA); }
+    st = autotune(c);
+    if (st != LQCD_OK) return fail(st);
     *out = c;
     return LQCD_OK;
 }
@@ -619,7 +626,8 @@ namespace {
 lqcd_status enqueue_chunk(lqcd_ctx* c, int nslots, int windowed) {
     const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
     for (int it = 0; it < CHECK_EVERY; ++it) {
-        CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->stream));
+        CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->stream,
+                              c->dslash_variant));
         if (windowed) {
             CK(launch_restart_coeffs(c->d_state, c->d_ptrs, nslots, c->eigwork, c->stream));
             CK(launch_window_gemm(c->kprec, 2 * c->nev, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
@@ -816,6 +824,31 @@ extern "C" lqcd_status lqcd_eigspace_get(lqcd_ctx* c, double* Ur, double* Ul, do
     return LQCD_OK;
 }
 
+namespace {
+
+// H = U_l^H A U_r and M = U_l^H U_r over the first n pairs, in FP64 arithmetic
+// (FP32-stored columns are converted to FP64 first), into Hout / Mout (ld).
+lqcd_status project_fp64(lqcd_ctx* c, int n, double2* Hout, double2* Mout, int ld) {
+    for (int j0 = 0; j0 < n; j0 += c->kmax) {
+        const int kb = std::min(c->kmax, n - j0);
+        const void* src = c->krylov(c->Ur, j0);
+        const void* in = src;
+        if (c->kprec) {
+            CK(launch_convert(src, 1, c->x_hi_all, 0, (size_t)kb * c->N, c->stream));
+            in = c->x_hi_all;
+        }
+        lqcd_status s = apply_fields(c, 0, 0, kb, in, c->kprec ? c->dbytes : c->kbytes, c->rt_all, c->dbytes, nullptr);
+        if (s != LQCD_OK) return s;
+        CK(launch_multidot(n, c->Ul, c->kprec, kb, c->rt_all, 0, c->N, Hout + j0, ld, 0, c->mdscratch,
+                           c->mdscratch_elems, c->stream));
+        CK(launch_multidot(n, c->Ul, c->kprec, kb, in, 0, c->N, Mout + j0, ld, 0, c->mdscratch,
+                           c->mdscratch_elems, c->stream));
+    }
+    return LQCD_OK;
+}
+
+}  // namespace
+
 extern "C" lqcd_status lqcd_eigspace_set(lqcd_ctx* c, int n, const double* Ur, const double* Ul) {
     if (!c || n < 0 || n > c->n_def_max) return LQCD_ERR_ARG;
     if (n > 0 && (!Ur || !Ul)) return LQCD_ERR_ARG;
@@ -826,23 +859,8 @@ extern "C" lqcd_status lqcd_eigspace_set(lqcd_ctx* c, int n, const double* Ur, c
     if (s != LQCD_OK) return s;
     s = upload(c, Ul, n, c->Ul, c->kprec, 0);
     if (s != LQCD_OK) return s;
-    // H = U_l^H A U_r, M = U_l^H U_r in FP64, in chunks of kmax columns
-    const int ld = c->n_def_max;
-    for (int j0 = 0; j0 < n; j0 += c->kmax) {
-        const int kb = std::min(c->kmax, n - j0);
-        const void* src = c->krylov(c->Ur, j0);
-        const void* in = src;
-        if (c->kprec) {
-            CK(launch_convert(src, 1, c->x_hi_all, 0, (size_t)kb * c->N, c->stream));
-            in = c->x_hi_all;
-        }
-        s = apply_fields(c, 0, 0, kb, in, c->kprec ? c->dbytes : c->kbytes, c->rt_all, c->dbytes, nullptr);
-        if (s != LQCD_OK) return s;
-        CK(launch_multidot(n, c->Ul, c->kprec, kb, c->rt_all, 0, c->N, c->Hdef + j0, ld, 0, c->mdscratch,
-                           c->mdscratch_elems, c->stream));
-        CK(launch_multidot(n, c->Ul, c->kprec, kb, src, c->kprec, c->N, c->Mdef + j0, ld, 0, c->mdscratch,
-                           c->mdscratch_elems, c->stream));
-    }
+    s = project_fp64(c, n, c->Hdef, c->Mdef, c->n_def_max);
+    if (s != LQCD_OK) return s;
     c->n_def = n;
     c->eig_rhs_done = c->p.n1;   // a loaded eigenspace counts as complete for LQCD_MODE_AUTO
     s = refactor(c);
@@ -864,12 +882,27 @@ extern "C" lqcd_status lqcd_eigs(lqcd_ctx* c, int* n_inout, double* evals, doubl
     double2* Y = G + (size_t)n * n;
     double2* Z = Y + (size_t)n * n;
     double2* lam = Z + (size_t)n * n;
-    copy_block_kernel<<<64, 256, 0, c->stream>>>(c->Hdef, ld, G, n, n, n);
+    // Pencil (U_l^H A U_r, U_l^H U_r) in FP64 arithmetic. With FP32-stored vectors
+    // the projections kept for deflation were summed in FP32, so recompute them.
+    const double2* Hp = c->Hdef;
+    const double2* Mp = c->Mlu;
+    const int* Mpiv = c->Mpiv;
+    int ldp = ld;
+    if (c->kprec) {
+        double2* Hr = c->dsmall + (size_t)MAX_SMALL * MAX_SMALL * 4;
+        double2* Mr = Hr + (size_t)n * n;
+        int* piv = c->dinfo + 24;
+        lqcd_status s = project_fp64(c, n, Hr, Mr, n);
+        if (s != LQCD_OK) return s;
+        CK(launch_lu_factor(n, Mr, n, piv, c->dinfo + 20, c->stream));
+        Hp = Hr; Mp = Mr; Mpiv = piv; ldp = n;
+    }
+    copy_block_kernel<<<64, 256, 0, c->stream>>>(Hp, ldp, G, n, n, n);
     count_launches(1);
     CK(cudaGetLastError());
-    CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 0, n, G, n, c->stream));
+    CK(launch_lu_solve(n, Mp, ldp, Mpiv, 0, n, G, n, c->stream));
     CK(launch_small_eig(n, G, n, n, lam, Y, Z, n, c->dinfo + 16, c->eigwork, c->stream));
-    CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 1, n, Z, n, c->stream));
+    CK(launch_lu_solve(n, Mp, ldp, Mpiv, 1, n, Z, n, c->stream));
     std::vector<double2> hl(n);
     CK(cudaMemcpyAsync(hl.data(), lam, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -892,7 +925,7 @@ extern "C" lqcd_status lqcd_eigs(lqcd_ctx* c, int* n_inout, double* evals, doubl
             // r_j = A u_j - lam_j u_j ; |r_j| / |u_j|
             lqcd_status s = apply_fields(c, 0, 0, kb, c->x_hi_all, c->dbytes, c->rt_all, c->dbytes, nullptr);
             if (s != LQCD_OK) return s;
-            double2* D = c->dsmall + (size_t)MAX_SMALL * MAX_SMALL * 4;
+            double2* D = c->dsmall + (size_t)MAX_SMALL * MAX_SMALL * 6;
             std::vector<double2> hd((size_t)kb * kb, make_double2(0, 0));
             for (int j = 0; j < kb; ++j) hd[(size_t)j * kb + j] = make_double2(-hl[j0 + j].x, -hl[j0 + j].y);
             CK(cudaMemcpyAsync(D, hd.data(), sizeof(double2) * kb * kb, cudaMemcpyHostToDevice, c->stream));
@@ -1005,9 +1038,9 @@ extern "C" lqcd_status lqcd_restart_coefficients(int m, int nev, const double* H
 // ============================================================ measurement
 extern "C" long long lqcd_kernel_launches(void) { return launches_so_far(); }
 
-extern "C" lqcd_status lqcd_time_kernel(lqcd_ctx* c, int kernel, int k, int reps, double* avg_ms) {
+static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, double* avg_ms) {
     if (!c || !avg_ms || k < 1 || k > c->kmax || reps < 1) return LQCD_ERR_ARG;
-    if (kernel < 0 || kernel > 3) return LQCD_ERR_ARG;
+    if (kernel < 0 || (kernel > 3 && kernel < 10) || kernel >= 10 + matvec_variants()) return LQCD_ERR_ARG;
     // Slots 0..k-1 iterate with fixed scalars on whatever their buffers hold.
     std::vector<SlotState> tmpl(c->kmax);
     for (int s = 0; s < c->kmax; ++s) {
@@ -1031,7 +1064,10 @@ extern "C" lqcd_status lqcd_time_kernel(lqcd_ctx* c, int kernel, int k, int reps
     for (int r = 0; r < reps; ++r) {
         CK(cudaMemcpyAsync(c->d_state, tmpl.data(), sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
         CK(cudaEventRecord(e0, c->stream));
-        if (kernel == 0) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->stream));
+        if (kernel == 0) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->stream,
+                                               c->dslash_variant));
+        else if (kernel >= 10) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k,
+                                                     c->stream, kernel - 10));
         else if (kernel == 1) CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
         else if (kernel == 2) CK(launch_bicg_direction(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
         else CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
@@ -1048,5 +1084,30 @@ extern "C" lqcd_status lqcd_time_kernel(lqcd_ctx* c, int kernel, int k, int reps
     CK(cudaMemcpyAsync(c->d_state, tmpl.data(), sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     *avg_ms = total / reps;
+    return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_time_kernel(lqcd_ctx* c, int kernel, int k, int reps, double* avg_ms) {
+    return time_kernel_impl(c, kernel, k, reps, avg_ms);
+}
+
+extern "C" int lqcd_dslash_variant(const lqcd_ctx* c) { return c ? c->dslash_variant : -1; }
+
+// Autotuner: time every operator-kernel variant on this lattice with a full
+// batch and keep the fastest (FP32 operator only; FP64 has one shape).
+static lqcd_status autotune(lqcd_ctx* c) {
+    if (!c->kprec) return LQCD_OK;
+    const int nv = matvec_variants();
+    c->tune_ms.assign(nv, 0.0);
+    double best = 1e300;
+    for (int v = 0; v < nv; ++v) {
+        double ms = 0.0;
+        lqcd_status s = time_kernel_impl(c, 10 + v, c->kmax, 1, &ms);   // warm-up
+        if (s != LQCD_OK) return s;
+        s = time_kernel_impl(c, 10 + v, c->kmax, 3, &ms);
+        if (s != LQCD_OK) return s;
+        c->tune_ms[v] = ms;
+        if (ms < best) { best = ms; c->dslash_variant = v; }
+    }
     return LQCD_OK;
 }

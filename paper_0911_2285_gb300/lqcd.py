@@ -98,6 +98,8 @@ def lib():
         L.lqcd_kernel_launches.restype = C.c_longlong
         L.lqcd_time_kernel.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
         L.lqcd_time_kernel.restype = C.c_int
+        L.lqcd_dslash_variant.argtypes = [vp]
+        L.lqcd_dslash_variant.restype = C.c_int
         for name in ("lqcd_eigbicg_init", "lqcd_solve", "lqcd_deflate", "lqcd_eigs", "lqcd_apply",
                      "lqcd_eigspace_get", "lqcd_eigspace_set", "lqcd_last_window", "lqcd_small_eig",
                      "lqcd_restart_coefficients"):
@@ -256,6 +258,10 @@ class Solver:
         ms = C.c_double()
         _check(lib().lqcd_time_kernel(self._h, int(kernel), int(k), int(reps), C.byref(ms)), "lqcd_time_kernel")
         return ms.value
+
+    def dslash_variant(self):
+        """Operator-kernel shape chosen by the autotuner."""
+        return lib().lqcd_dslash_variant(self._h)
 
     def eigspace_size(self):
         return lib().lqcd_eigspace_size(self._h)
