@@ -86,7 +86,8 @@ typedef struct {
     int k_max;                /* right-hand sides per batched launch (1..8); 0 = 8 */
     size_t hbm_budget_bytes;  /* 0 = no limit; init fails with LQCD_ERR_OOM above it */
     int n_def_max;            /* eigenspace capacity in vectors (<= 80); 0 = min(80, n1*nev) */
-    double delta;             /* reliable-update trigger ||r|| < delta * max||r|| (MIXED); 0 = 0.1 */
+    double delta;             /* MIXED reliable update when ||r|| < delta * ||r at the last update||
+                                 (or < 1e-3 * max||r|| since then); 0 = 0.01 */
 } lqcd_params;
 
 typedef struct {

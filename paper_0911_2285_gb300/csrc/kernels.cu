@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
         st.bnorm = sqrt(tot[1].y);
         st.rhat_norm = st.rnorm;
         st.rmax = st.rnorm;
+        st.r_ru = st.rnorm;
         st.true_rnorm = st.rnorm;
         st.iter = 0; st.vs = 0; st.need_ru = 0; st.ru_count = 0; st.restarts = 0; st.restart_r = 0;
         st.matvecs = 1; st.live = 1;
@@ -421,17 +422,21 @@ __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, c
         if (!isfinite(st.rnorm_new) || !isfinite(st.rho_new.x) || !isfinite(st.rho_new.y)) {
             st.status = ST_BREAKDOWN;
         } else {
+            // Reliable update (FP32 Krylov vectors): when the residual has dropped by
+            // delta since the last update, or far below the largest residual seen
+            // since then (the recursion's rounding error scales with that maximum);
+            // and always to confirm convergence.
             if (st.rnorm_new <= st.tol * st.bnorm) st.need_ru = 1;
-            if (st.delta > 0.0 && st.rnorm_new < st.delta * st.rmax) st.need_ru = 1;
             if (st.rnorm_new > st.rmax) st.rmax = st.rnorm_new;
+            if (st.delta > 0.0 && (st.rnorm_new < st.delta * st.r_ru || st.rnorm_new < 1e-3 * st.rmax)) st.need_ru = 1;
         }
     }
 }
 
-// FP64 true residual r = b - A (x_hi + x_lo) for slots that asked for it.
+// FP64 true residual r = b - A x_hi for slots that asked for it (x_lo has been
+// folded into x_hi just before).
 // check_only = 0: inside the iteration (converged if ||r|| <= tol ||b||);
 // check_only = 1: final report for every slot that was started.
-template <typename S>
 __global__ void __launch_bounds__(DS_THREADS) true_resid_kernel(Geom g, const void* links64, double kappa,
                                                                 SlotState* states, const SlotPtrs* ptrs,
                                                                 int check_only) {
@@ -443,7 +448,7 @@ __global__ void __launch_bounds__(DS_THREADS) true_resid_kernel(Geom g, const vo
         return;
     }
     LinksD U{reinterpret_cast<const double2*>(links64), g.V};
-    SumIn<S> in{P.x_hi, P.x_lo, g.V};
+    FieldIn<double> in{P.x_hi, g.V};
     double2 v[1] = {make_double2(0, 0)};
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
         double2 acc[12], self[12], b[12];
@@ -465,8 +470,25 @@ __global__ void __launch_bounds__(DS_THREADS) true_resid_kernel(Geom g, const vo
     }
 }
 
-// Reliable update: x_hi += x_lo, x_lo = 0; unless converged, the recursive
-// residual r_j is replaced by the true one and rho_j recomputed.
+// Reliable update, first half: x_hi += x_lo, x_lo = 0 for slots that asked for it.
+template <typename S>
+__global__ void __launch_bounds__(BL_THREADS) fold_ru_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    const SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (st.status != ST_RUNNING || !st.need_ru) return;
+    const size_t units = N / 2;
+    Unit<S> zero{mk<S>(0, 0), mk<S>(0, 0)};
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+        Unit<double> xh = Unit<double>::load(P.x_hi, u);
+        Unit<S> xl = Unit<S>::load(P.x_lo, u);
+        xh.a = xh.a + to_d(xl.a); xh.b = xh.b + to_d(xl.b);
+        xh.store(P.x_hi, u);
+        zero.store(P.x_lo, u);
+    }
+}
+
+// Reliable update, second half: unless converged, the recursive residual r_j is
+// replaced by the true one and rho_j recomputed.
 template <typename S>
 __global__ void __launch_bounds__(BL_THREADS) replace_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
     SlotState& st = states[blockIdx.y];
@@ -477,13 +499,7 @@ __global__ void __launch_bounds__(BL_THREADS) replace_kernel(SlotState* states, 
     const void* hcur = slot_field<S>(P.W, next_slot(st), N);
     cplx<S> rho = mk<S>(S(0), S(0));
     const size_t units = N / 2;
-    Unit<S> zero{mk<S>(0, 0), mk<S>(0, 0)};
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
-        Unit<double> xh = Unit<double>::load(P.x_hi, u);
-        Unit<S> xl = Unit<S>::load(P.x_lo, u);
-        xh.a = xh.a + to_d(xl.a); xh.b = xh.b + to_d(xl.b);
-        xh.store(P.x_hi, u);
-        zero.store(P.x_lo, u);
         if (run) {
             Unit<double> rt = Unit<double>::load(P.r_true, u);
             Unit<S> r{cvt<S>(rt.a), cvt<S>(rt.b)};
@@ -499,6 +515,7 @@ __global__ void __launch_bounds__(BL_THREADS) replace_kernel(SlotState* states, 
             st.rho_new = tot[0];
             st.rnorm_new = st.true_rnorm;
             st.rmax = st.true_rnorm;
+            st.r_ru = st.true_rnorm;
         }
         st.need_ru = 0;
         st.ru_count += 1;
@@ -773,7 +790,7 @@ static void matvec_launch(const Geom& g, const void* links, double kappa, SlotSt
     matvec_kernel<S, THREADS, MINB, PAIR><<<nb * njobs, THREADS, 0, s>>>(g, links, kappa, states, ptrs, njobs);
 }
 
-int matvec_variants() { return 5; }
+int matvec_variants() { return 10; }
 
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
                                const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant) {
@@ -785,6 +802,11 @@ cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, i
             case 2: matvec_launch<float, 256, 3, false>(g, links, kappa, states, ptrs, nslots, s); break;
             case 3: matvec_launch<float, 128, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
             case 4: matvec_launch<float, 128, 4, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 5: matvec_launch<float, 128, 4, false>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 6: matvec_launch<float, 128, 5, false>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 7: matvec_launch<float, 128, 3, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 8: matvec_launch<float, 256, 2, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 9: matvec_launch<float, 64, 8, false>(g, links, kappa, states, ptrs, nslots, s); break;
             default: matvec_launch<float, 128, 1, false>(g, links, kappa, states, ptrs, nslots, s); break;
         }
     }
@@ -802,13 +824,15 @@ cudaError_t launch_bicg_update(int prec, SlotState* states, const SlotPtrs* ptrs
 
 cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int prec, SlotState* states,
                            const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s) {
+    dim3 g2(blas_blocks(N / 2), nslots);
+    if (prec == 0) fold_ru_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
+    else fold_ru_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
+    count_launches(1);
     dim3 grid(ds_blocks(g.V), nslots);
-    if (prec == 0) true_resid_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 0);
-    else true_resid_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 0);
+    true_resid_kernel<<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 0);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 g2(blas_blocks(N / 2), nslots);
     if (prec == 0) replace_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     else replace_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     count_launches(1);
@@ -839,8 +863,7 @@ cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 grid(ds_blocks(g.V), nslots);
-    if (prec == 0) true_resid_kernel<double><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 1);
-    else true_resid_kernel<float><<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 1);
+    true_resid_kernel<<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 1);
     count_launches(1);
     return cudaGetLastError();
 }

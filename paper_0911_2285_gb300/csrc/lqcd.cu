@@ -222,7 +222,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     lqcd_ctx* c = new lqcd_ctx();
     c->p = *params;
     if (c->p.k_max == 0) c->p.k_max = MAX_SLOTS;
-    if (c->p.delta == 0.0) c->p.delta = 0.1;
+    if (c->p.delta == 0.0) c->p.delta = 0.01;
     c->kmax = c->p.k_max;
     c->m = c->p.m;
     c->nev = c->p.nev;
@@ -1052,7 +1052,7 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
         st.tol = 0.0;
         st.maxiter = 1 << 30;
         st.rho = make_double2(1.0, 0.0);
-        st.rnorm = 1.0; st.bnorm = 1.0; st.rmax = 1.0;
+        st.rnorm = 1.0; st.bnorm = 1.0; st.rmax = 1.0; st.r_ru = 1.0;
         st.alpha = make_double2(0.1, 0.0);
         st.beta = make_double2(0.1, 0.0);
     }

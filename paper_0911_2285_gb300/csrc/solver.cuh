@@ -21,6 +21,7 @@ struct SlotState {
     double rnorm_new;     // ||r_j||
     double bnorm;
     double rmax;          // largest ||r|| since the last reliable update
+    double r_ru;          // ||r|| at the last reliable update (or the start)
     double true_rnorm;    // last FP64 ||b - A x||
     double tol;           // relative tolerance
     double delta;         // reliable-update factor (0: only at convergence)
