@@ -342,7 +342,8 @@ def main_ours(args):
         "roofline": {"bound": "hbm", "kernel": "operator pair A p, A^+ phat (FP32, k=8 batch)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": "measured" if peaks else "fallback", "traffic": traffic,
-                     "algorithmic_bytes_per_launch": alg_bytes, "ms_per_launch": op_ms},
+                     "algorithmic_bytes_per_launch": alg_bytes, "ms_per_launch": op_ms,
+                     "kernel_shape": s.dslash_variant()},
         "kernel_ms": {"dhop_pair": op_ms, "update": upd_ms, "direction": dir_ms},
         "cpu_baseline": cpu,
         "clocks": clk,

@@ -50,6 +50,19 @@ cudaError_t launch_scale_fields(int b, void* Y, int yprec, const double2* sc, si
 // BiCG iteration kernels over nslots slots (see kernels.cu for the contract).
 cudaError_t launch_bicg_start(const Geom& g, const void* links, double kappa, int prec,
                               SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+// Plane-streaming operator pair (dslash_tiled.cu): YB rows per CTA tile, nyb
+// tiles along y, t segments of tseg planes (nseg of them), nslots batch slots.
+struct TileGeom {
+    int YB, nyb, tseg, nseg, nslots;
+};
+// Plan a tiling for this lattice and batch; false if the lattice does not tile.
+bool tiled_plan(const Geom& g, int nslots, TileGeom* tg);
+size_t tiled_smem_bytes(int Lx, int YB);
+cudaError_t prepare_tiled_kernel();
+// err: device word set to 1 if a bounded wait timed out.
+cudaError_t launch_matvec_tiled(const Geom& g, const TileGeom& tg, const void* links32, double kappa,
+                                SlotState* states, const SlotPtrs* ptrs, int* err, cudaStream_t s);
+
 // variant: operator-kernel shape chosen by the autotuner (0 .. matvec_variants()-1)
 int matvec_variants();
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec,

@@ -42,6 +42,7 @@ void set_error(const char* what, cudaError_t e) {
     } while (0)
 
 constexpr int CHECK_EVERY = 8;   // iterations per graph launch / status poll
+constexpr int TILED = 100;       // dslash_variant value of the plane-streaming kernel
 
 }  // namespace
 
@@ -97,7 +98,10 @@ struct lqcd_ctx {
     int* dinfo = nullptr;
     double2* dconst = nullptr;      // constants
 
-    int dslash_variant = 0;         // operator-kernel shape (autotuned at init)
+    int dslash_variant = 0;         // operator-kernel shape (autotuned at init); TILED = plane streaming
+    TileGeom tgeo[MAX_SLOTS + 1] = {};
+    bool tile_ok[MAX_SLOTS + 1] = {};
+    int* d_err = nullptr;           // device error word of the bounded waits
     std::vector<double> tune_ms;    // autotuner timings per variant
 
     // CUDA graphs of CHECK_EVERY iterations, keyed by (nslots, windowed)
@@ -297,12 +301,14 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     AL(c->dsmall, (size_t)(MAX_SMALL * MAX_SMALL * 6 + 4096) * 16);
     AL(c->dinfo, (64 + MAX_SMALL) * sizeof(int));
     AL(c->dconst, 64 * 16);
+    AL(c->d_err, 16);
 #undef AL
     if ((e = cudaMemset(c->counters, 0, K * CNT_COUNT * sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemset(c->small_all, 0, K * c->small_stride * 16)) != cudaSuccess ||
         (e = cudaMemset(c->win_all, 0, K * 2 * (c->m + 1) * c->kbytes)) != cudaSuccess ||
         (e = cudaMemset(c->vec_all, 0, K * 6 * c->kbytes)) != cudaSuccess ||
-        (e = cudaMemset(c->x_lo_all, 0, K * c->kbytes)) != cudaSuccess) {
+        (e = cudaMemset(c->x_lo_all, 0, K * c->kbytes)) != cudaSuccess ||
+        (e = cudaMemset(c->d_err, 0, 16)) != cudaSuccess) {
         set_error("cudaMemset", e);
         return fail(LQCD_ERR_CUDA);
     }
@@ -332,6 +338,8 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     c->last_vs.assign(c->kmax, 0);
     c->last_restarts.assign(c->kmax, 0);
     if ((e = prepare_eig_kernels()) != cudaSuccess) { set_error("prepare_eig_kernels", e); return fail(LQCD_ERR_CUDA); }
+    if ((e = prepare_tiled_kernel()) != cudaSuccess) { set_error("prepare_tiled_kernel", e); return fail(LQCD_ERR_CUDA); }
+    for (int n = 1; n <= c->kmax; ++n) c->tile_ok[n] = c->kprec && tiled_plan(c->g, n, &c->tgeo[n]);
     st = autotune(c);
     if (st != LQCD_OK) return fail(st);
     *out = c;
@@ -622,12 +630,21 @@ extern "C" lqcd_status lqcd_deflate(lqcd_ctx* c, int k, const double* b, double*
 // ============================================================ the solve
 namespace {
 
+// The operator pair of one iteration in the autotuned kernel shape.
+cudaError_t launch_matvec(lqcd_ctx* c, int nslots, int variant) {
+    if (variant == TILED && c->tile_ok[nslots])
+        return launch_matvec_tiled(c->g, c->tgeo[nslots], c->links32, c->p.kappa, c->d_state, c->d_ptrs, c->d_err,
+                                   c->stream);
+    const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
+    return launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->stream,
+                              variant == TILED ? 0 : variant);
+}
+
 // One chunk of CHECK_EVERY iterations for nslots slots (graph body).
 lqcd_status enqueue_chunk(lqcd_ctx* c, int nslots, int windowed) {
     const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
     for (int it = 0; it < CHECK_EVERY; ++it) {
-        CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->stream,
-                              c->dslash_variant));
+        CK(launch_matvec(c, nslots, c->dslash_variant));
         if (windowed) {
             CK(launch_restart_coeffs(c->d_state, c->d_ptrs, nslots, c->eigwork, c->stream));
             CK(launch_window_gemm(c->kprec, 2 * c->nev, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
@@ -682,8 +699,18 @@ lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol) {
     if (s != LQCD_OK) return s;
     CK(launch_bicg_start(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
     while (true) {
+        int herr = 0;
         CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SlotState) * k, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        if (herr) {
+            // a bounded device wait gave up: the reduction counters may be stale
+            CK(cudaMemsetAsync(c->counters, 0, (size_t)c->kmax * CNT_COUNT * sizeof(unsigned), c->stream));
+            CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            g_last_error = "operator kernel: bounded wait on a TMA copy timed out";
+            return LQCD_ERR_TIMEOUT;
+        }
         bool any = false;
         for (int j = 0; j < k; ++j) any = any || c->h_state[j].status == ST_RUNNING;
         if (!any) break;
@@ -1040,7 +1067,8 @@ extern "C" long long lqcd_kernel_launches(void) { return launches_so_far(); }
 
 static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, double* avg_ms) {
     if (!c || !avg_ms || k < 1 || k > c->kmax || reps < 1) return LQCD_ERR_ARG;
-    if (kernel < 0 || (kernel > 3 && kernel < 10) || kernel >= 10 + matvec_variants()) return LQCD_ERR_ARG;
+    if (kernel < 0 || (kernel > 3 && kernel < 10) || (kernel >= 10 + matvec_variants() && kernel != 20)) return LQCD_ERR_ARG;
+    if (kernel == 20 && !c->tile_ok[k]) return LQCD_ERR_ARG;
     // Slots 0..k-1 iterate with fixed scalars on whatever their buffers hold.
     std::vector<SlotState> tmpl(c->kmax);
     for (int s = 0; s < c->kmax; ++s) {
@@ -1066,6 +1094,7 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
         CK(cudaEventRecord(e0, c->stream));
         if (kernel == 0) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->stream,
                                                c->dslash_variant));
+        else if (kernel == 20) CK(launch_matvec(c, k, TILED));
         else if (kernel >= 10) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k,
                                                      c->stream, kernel - 10));
         else if (kernel == 1) CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
@@ -1109,5 +1138,70 @@ static lqcd_status autotune(lqcd_ctx* c) {
         c->tune_ms[v] = ms;
         if (ms < best) { best = ms; c->dslash_variant = v; }
     }
+    if (c->tile_ok[c->kmax]) {
+        double ms = 0.0;
+        lqcd_status s = time_kernel_impl(c, 20, c->kmax, 1, &ms);
+        if (s != LQCD_OK) return s;
+        s = time_kernel_impl(c, 20, c->kmax, 3, &ms);
+        if (s != LQCD_OK) return s;
+        c->tune_ms.push_back(ms);
+        if (ms < best) { best = ms; c->dslash_variant = TILED; }
+    }
+    int herr = 0;
+    CK(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+        // the plane-streaming kernel timed out on a copy: never use it on this context
+        CK(cudaMemset(c->d_err, 0, sizeof(int)));
+        CK(cudaMemset(c->counters, 0, (size_t)c->kmax * CNT_COUNT * sizeof(unsigned)));
+        for (int n = 0; n <= MAX_SLOTS; ++n) c->tile_ok[n] = false;
+        if (c->dslash_variant == TILED) c->dslash_variant = 0;
+    }
+    return LQCD_OK;
+}
+
+// ============================================================ pair-kernel hook
+extern "C" lqcd_status lqcd_apply_pair(lqcd_ctx* c, int variant, int k, const double* p, const double* phat,
+                                       double* Ap, double* Ahp, double* sigma) {
+    if (!c || !p || !phat || !Ap || !Ahp || k < 1 || k > c->kmax) return LQCD_ERR_ARG;
+    if (variant == TILED) {
+        if (!c->tile_ok[k]) return LQCD_ERR_ARG;
+    } else if (variant < 0 || variant >= matvec_variants() || (!c->kprec && variant != 0)) {
+        return LQCD_ERR_ARG;
+    }
+    const size_t fb = 2 * c->N;   // doubles per host field
+    for (int s = 0; s < k; ++s) {
+        lqcd_status r = upload(c, p + s * fb, 1, c->h_ptrs[s].p, c->kprec, 0);
+        if (r != LQCD_OK) return r;
+        r = upload(c, phat + s * fb, 1, c->h_ptrs[s].phat, c->kprec, 0);
+        if (r != LQCD_OK) return r;
+    }
+    std::vector<SlotState> tmpl(c->kmax);
+    for (int s = 0; s < c->kmax; ++s) {
+        memset(&tmpl[s], 0, sizeof(SlotState));
+        tmpl[s].status = s < k ? ST_RUNNING : ST_IDLE;
+        tmpl[s].rho = make_double2(1.0, 0.0);
+    }
+    CK(cudaMemcpyAsync(c->d_state, tmpl.data(), sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_matvec(c, k, variant));
+    std::vector<SlotState> out(c->kmax);
+    int herr = 0;
+    CK(cudaMemcpyAsync(out.data(), c->d_state, sizeof(SlotState) * c->kmax, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    for (int s = 0; s < k; ++s) {
+        lqcd_status r = download(c, c->h_ptrs[s].Ap[0], c->kprec, 1, Ap + s * fb, 0);
+        if (r != LQCD_OK) return r;
+        r = download(c, c->h_ptrs[s].Ahp[0], c->kprec, 1, Ahp + s * fb, 0);
+        if (r != LQCD_OK) return r;
+    }
+    for (int s = 0; s < c->kmax; ++s) { tmpl[s].status = ST_IDLE; }
+    CK(cudaMemcpyAsync(c->d_state, tmpl.data(), sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (herr) {
+        CK(cudaMemset(c->d_err, 0, sizeof(int)));
+        CK(cudaMemset(c->counters, 0, (size_t)c->kmax * CNT_COUNT * sizeof(unsigned)));
+        return LQCD_ERR_TIMEOUT;
+    }
+    if (sigma)
+        for (int s = 0; s < k; ++s) { sigma[2 * s] = out[s].sigma.x; sigma[2 * s + 1] = out[s].sigma.y; }
     return LQCD_OK;
 }

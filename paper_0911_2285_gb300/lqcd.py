@@ -98,6 +98,8 @@ def lib():
         L.lqcd_kernel_launches.restype = C.c_longlong
         L.lqcd_time_kernel.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
         L.lqcd_time_kernel.restype = C.c_int
+        L.lqcd_apply_pair.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
+        L.lqcd_apply_pair.restype = C.c_int
         L.lqcd_dslash_variant.argtypes = [vp]
         L.lqcd_dslash_variant.restype = C.c_int
         for name in ("lqcd_eigbicg_init", "lqcd_solve", "lqcd_deflate", "lqcd_eigs", "lqcd_apply",
@@ -258,6 +260,19 @@ class Solver:
         ms = C.c_double()
         _check(lib().lqcd_time_kernel(self._h, int(kernel), int(k), int(reps), C.byref(ms)), "lqcd_time_kernel")
         return ms.value
+
+    def apply_pair(self, p, phat, variant):
+        """One launch of the operator-pair kernel shape ``variant``: ``(A p, A^+ phat, sigma)``."""
+        p = np.ascontiguousarray(p, dtype=np.complex128).reshape(-1, self.n)
+        phat = np.ascontiguousarray(phat, dtype=np.complex128).reshape(-1, self.n)
+        k = p.shape[0]
+        ap = np.zeros_like(p)
+        ahp = np.zeros_like(phat)
+        sig = np.zeros(k, dtype=np.complex128)
+        _check(lib().lqcd_apply_pair(self._h, int(variant), k, C.c_void_p(p.ctypes.data), C.c_void_p(phat.ctypes.data),
+                                     C.c_void_p(ap.ctypes.data), C.c_void_p(ahp.ctypes.data),
+                                     C.c_void_p(sig.ctypes.data)), "lqcd_apply_pair")
+        return ap, ahp, sig
 
     def dslash_variant(self):
         """Operator-kernel shape chosen by the autotuner."""

@@ -59,3 +59,24 @@ def test_apply_full_size_24x24x24x64_sampled():
         assert np.abs(out - ref).max() <= 1e-14 * np.abs(ref).max()
         out32 = s.apply(v, precision="mixed")[0]
         assert rel(out32, ref) <= 2e-6
+
+
+@pytest.mark.parametrize("name", ["8^4", "16^3x32"])
+def test_operator_pair_kernels_match_oracle(name):
+    """Every shape of the BiCG operator-pair kernel (the autotuner's candidates,
+    including the TMA plane-streaming one): A p, A^+ phat and sigma = (phat, A p)
+    against the oracle, FP32 fields, batches of 1 and 3."""
+    from paper_0911_2285_gb300 import Solver
+    w, links, op = workload(name)
+    with Solver(links, w["dims"], w["kappa"], nev=1, m=3, precision="mixed", k_max=3, n_def_max=1) as s:
+        for k in (1, 3):
+            p = np.stack([random_field(op.n, 20 + i) for i in range(k)])
+            ph = np.stack([random_field(op.n, 40 + i) for i in range(k)])
+            refs = [(op.apply(p[i]), op.apply_dag(ph[i])) for i in range(k)]
+            for variant in list(range(10)) + [100]:
+                ap, ahp, sig = s.apply_pair(p, ph, variant)
+                for i in range(k):
+                    assert rel(ap[i], refs[i][0]) <= 2e-6, (variant, i)
+                    assert rel(ahp[i], refs[i][1]) <= 2e-6, (variant, i)
+                    sref = np.vdot(ph[i], refs[i][0])
+                    assert abs(sig[i] - sref) <= 1e-5 * abs(sref), (variant, i)
