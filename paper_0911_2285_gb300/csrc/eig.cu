@@ -22,15 +22,18 @@ constexpr double EPS = 2.220446049250313e-16;
 __device__ __forceinline__ double2 czero() { return make_double2(0.0, 0.0); }
 __device__ __forceinline__ double2 cone() { return make_double2(1.0, 0.0); }
 
-// Givens G = [[c, s], [-conj(s), c]] with G [x; y] = [r; 0].
-__device__ __forceinline__ void givens(double2 x, double2 y, double& c, double2& s) {
-    double ax = cabs_(x), ay = cabs_(y);
-    if (ay == 0.0) { c = 1.0; s = czero(); return; }
-    if (ax == 0.0) { c = 0.0; s = cone(); return; }
-    double nrm = hypot(ax, ay);
-    c = ax / nrm;
-    double2 ph = make_double2(x.x / ax, x.y / ax);
-    s = (1.0 / nrm) * (ph * conj_(y));
+// |re| + |im|: the modulus surrogate used for negligibility tests (no sqrt).
+__device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+
+// Unitary rotation G = [[cx, cy], [-conj(cy), conj(cx)]] with G [x; y] = [n; 0],
+// cx = conj(x)/n, cy = conj(y)/n, n = sqrt(|x|^2 + |y|^2): one square root and one
+// reciprocal (FP64 divide and sqrt are long sequences on this GPU).
+__device__ __forceinline__ void givens(double2 x, double2 y, double2& cx, double2& cy) {
+    const double n2 = cabs2(x) + cabs2(y);
+    if (n2 == 0.0) { cx = cone(); cy = czero(); return; }
+    const double inv = 1.0 / sqrt(n2);
+    cx = inv * conj_(x);
+    cy = inv * conj_(y);
 }
 
 // ---------------------------------------------------------------------------
@@ -96,8 +99,7 @@ __device__ int schur(double2* A, double2* Q, int n, int lda, double2* v /* n */,
     const double anorm = sh[4] > 0.0 ? sh[4] : 1.0;
     // Single-shift implicit QR with deflation from the bottom.
     __shared__ int s_l, s_hi, s_fail;
-    __shared__ double s_c;
-    __shared__ double2 s_s, s_mu;
+    __shared__ double2 s_cx, s_cy, s_mu;
     if (tid == 0) { s_hi = n - 1; s_fail = 0; }
     __syncthreads();
     int iters = 0, total = 0;
@@ -106,9 +108,9 @@ __device__ int schur(double2* A, double2* Q, int n, int lda, double2* v /* n */,
             int hi = s_hi;
             int l = hi;
             while (l > 0) {
-                double tst = cabs_(A[(l - 1) * lda + l - 1]) + cabs_(A[l * lda + l]);
+                double tst = cabs1(A[(l - 1) * lda + l - 1]) + cabs1(A[l * lda + l]);
                 if (tst == 0.0) tst = anorm;
-                if (cabs_(A[l * lda + l - 1]) <= EPS * tst) { A[l * lda + l - 1] = czero(); break; }
+                if (cabs1(A[l * lda + l - 1]) <= EPS * tst) { A[l * lda + l - 1] = czero(); break; }
                 --l;
             }
             s_l = l;
@@ -131,7 +133,7 @@ __device__ int schur(double2* A, double2* Q, int n, int lda, double2* v /* n */,
             double2 mu;
             if (iters % 11 == 10) {
                 // exceptional shift
-                mu = d + make_double2(0.75 * cabs_(c), 0.0);
+                mu = d + make_double2(0.75 * cabs1(c), 0.0);
             } else {
                 double2 t = 0.5 * (a - d);
                 double2 bc = b * c;
@@ -155,28 +157,28 @@ __device__ int schur(double2* A, double2* Q, int n, int lda, double2* v /* n */,
                 double2 x, y;
                 if (k == l) { x = A[l * lda + l] - mu; y = A[(l + 1) * lda + l]; }
                 else { x = A[k * lda + k - 1]; y = A[(k + 1) * lda + k - 1]; }
-                double c; double2 s;
-                givens(x, y, c, s);
-                s_c = c; s_s = s;
+                double2 cx, cy;
+                givens(x, y, cx, cy);
+                s_cx = cx; s_cy = cy;
             }
             __syncthreads();
-            const double c = s_c;
-            const double2 s = s_s;
-            // rows k, k+1
+            const double2 cx = s_cx, cy = s_cy;
+            const double2 cxc = conj_(cx), cyc = conj_(cy);
+            // rows k, k+1:  [a; b] <- G [a; b]
             const int j0 = (k == l) ? l : k - 1;
             for (int j = j0 + tid; j < n; j += blockDim.x) {
                 double2 a = A[k * lda + j], b = A[(k + 1) * lda + j];
-                A[k * lda + j] = c * a + s * b;
-                A[(k + 1) * lda + j] = c * b - conj_(s) * a;
+                A[k * lda + j] = cx * a + cy * b;
+                A[(k + 1) * lda + j] = cxc * b - cyc * a;
             }
             __syncthreads();
-            // columns k, k+1 of A (rows 0..min(k+2, hi)) and of Q (all rows)
+            // columns k, k+1 of A (rows 0..min(k+2, hi)) and of Q (all rows):  [a, b] <- [a, b] G^H
             const int i1 = min(k + 2, hi);
             for (int i = tid; i < (i1 + 1) + n; i += blockDim.x) {
                 double2* row = i <= i1 ? A + i * lda : Q + (i - i1 - 1) * lda;
                 double2 a = row[k], b = row[k + 1];
-                row[k] = c * a + conj_(s) * b;
-                row[k + 1] = c * b - s * a;
+                row[k] = a * cxc + b * cyc;
+                row[k + 1] = b * cx - a * cy;
             }
             __syncthreads();
             if (k > l && tid == 0) A[(k + 1) * lda + k - 1] = czero();
@@ -192,15 +194,16 @@ __device__ int schur(double2* A, double2* Q, int n, int lda, double2* v /* n */,
 // Order of the eigenvalues on the diagonal of T: smallest |lambda|, then Im.
 __device__ void order_eigs(const double2* T, int n, int lda, int* ord) {
     if (threadIdx.x == 0) {
+        // squared moduli order the same way as moduli (ties included)
         for (int i = 0; i < n; ++i) ord[i] = i;
         for (int i = 1; i < n; ++i) {
             int key = ord[i];
             double2 lk = T[key * lda + key];
-            double ak = cabs_(lk);
+            double ak = cabs2(lk);
             int j = i - 1;
             while (j >= 0) {
                 double2 lj = T[ord[j] * lda + ord[j]];
-                double aj = cabs_(lj);
+                double aj = cabs2(lj);
                 bool after = (aj > ak) || (aj == ak && lj.y > lk.y);
                 if (!after) break;
                 ord[j + 1] = ord[j];
@@ -233,9 +236,9 @@ __device__ void eigvecs(const double2* T, const double2* Q, int n, int lda, cons
                 double2 sacc = czero();
                 for (int l = j + 1; l <= k; ++l) sacc = sacc + T[j * lda + l] * w[l];
                 double2 d = T[j * lda + j] - lam;
-                if (cabs_(d) < smin) d = make_double2(smin, 0.0);
-                w[j] = -cdiv(sacc, d);
-                if (cabs_(w[j]) > 1e150) {
+                if (cabs1(d) < smin) d = make_double2(smin, 0.0);
+                w[j] = -((1.0 / cabs2(d)) * (sacc * conj_(d)));
+                if (cabs1(w[j]) > 1e150) {
                     for (int l = j; l <= k; ++l) w[l] = 1e-150 * w[l];
                 }
             }
@@ -244,9 +247,9 @@ __device__ void eigvecs(const double2* T, const double2* Q, int n, int lda, cons
                 double2 sacc = czero();
                 for (int l = k; l < j; ++l) sacc = sacc + w[l] * T[l * lda + j];
                 double2 d = T[j * lda + j] - lam;
-                if (cabs_(d) < smin) d = make_double2(smin, 0.0);
-                w[j] = -cdiv(sacc, d);
-                if (cabs_(w[j]) > 1e150) {
+                if (cabs1(d) < smin) d = make_double2(smin, 0.0);
+                w[j] = -((1.0 / cabs2(d)) * (sacc * conj_(d)));
+                if (cabs1(w[j]) > 1e150) {
                     for (int l = k; l <= j; ++l) w[l] = 1e-150 * w[l];
                 }
             }
@@ -332,39 +335,47 @@ __global__ void __launch_bounds__(ET) small_eig_kernel(int n, const double2* Ain
 // ------------------------------------------------------- BiCG-eigen (coeffs)
 // Work arrays (global, per problem) for the restart coefficient computation.
 struct RestartWork {
-    double2 *y1, *z1, *y2, *z2, *HY, *T, *u, *q, *W1, *W2, *lamtmp, *M;
+    double2 *y1, *z1, *y2, *z2, *HY, *T, *u, *q, *W1, *W2, *lamtmp, *lamtmp2, *M;
     int *rowp, *colp;
     static size_t elems(int m, int nev) {
         const int r = 2 * nev;
-        return (size_t)m * nev * 4 + (size_t)m * r + (size_t)r * r * 3 + (size_t)m * m * 2 + m + (size_t)nev * nev + 64;
+        return (size_t)m * nev * 4 + (size_t)m * r + (size_t)r * r * 3 + (size_t)m * m * 2 + 2 * m + (size_t)nev * nev + 64;
     }
     __device__ RestartWork(double2* base, int m, int nev) {
         const int r = 2 * nev;
         y1 = base; z1 = y1 + m * nev; y2 = z1 + m * nev; z2 = y2 + m * nev;
         HY = z2 + m * nev; T = HY + m * r; u = T + r * r; q = u + r * r;
-        W1 = q + r * r; W2 = W1 + m * m; lamtmp = W2 + m * m; M = lamtmp + m;
+        W1 = q + r * r; W2 = W1 + m * m; lamtmp = W2 + m * m; lamtmp2 = lamtmp + m; M = lamtmp2 + m;
         rowp = reinterpret_cast<int*>(M + nev * nev);
         colp = rowp + 32;
     }
 };
 
-// Algorithm BiCG-eigen in coefficient space for H (m x m, ld = ldh, global).
-// Writes Yc, Zc ((m) x r, ld = ldc), lam (r); returns r (0 on failure).
-__device__ int restart_coeffs_block(const double2* H, int ldh, int m, int nev, double2* Yc, double2* Zc,
-                                    int ldc, double2* lam, EigSmem& S, RestartWork& Wk, int* fail_out) {
+// Algorithm BiCG-eigen in coefficient space, first part: which = 0 computes
+// eig(H^(m)) -> y1, z1 (nev smallest); which = 1 computes eig(H^(m-1)) -> y2, z2,
+// padded with a zero row. The two parts use disjoint scratch, so two CTAs can
+// run them at the same time.
+__device__ int restart_eigs_part(const double2* H, int ldh, int m, int nev, int which, EigSmem& S,
+                                 RestartWork& Wk) {
+    const int tid = threadIdx.x;
+    const int n = which ? m - 1 : m;
+    for (int e = tid; e < n * n; e += blockDim.x) S.A[e] = H[(e / n) * ldh + (e % n)];
+    __syncthreads();
+    double2* scratch = which ? Wk.W2 : Wk.W1;   // 2 n nev <= m^2
+    int fail = eig_block(S.A, S.Q, n, n, nev, which ? Wk.lamtmp2 : Wk.lamtmp, which ? Wk.y2 : Wk.y1,
+                         which ? Wk.z2 : Wk.z1, nev, scratch, scratch + (size_t)n * nev, S.v, S.sh, S.ord);
+    if (which)
+        for (int i = tid; i < nev; i += blockDim.x) { Wk.y2[(m - 1) * nev + i] = czero(); Wk.z2[(m - 1) * nev + i] = czero(); }
+    __syncthreads();
+    return fail;
+}
+
+// Second part: bi-orthogonalize, T = zt^H H yt, eig(T), Yc = yt u, Zc = zt q.
+// Writes Yc, Zc (m x r, ld = ldc), lam (r); returns r.
+__device__ int restart_finish_part(const double2* H, int ldh, int m, int nev, double2* Yc, double2* Zc, int ldc,
+                                   double2* lam, EigSmem& S, RestartWork& Wk, int* fail_out) {
     const int tid = threadIdx.x;
     int fail = 0;
-    // 1. eig(H^(m)), nev smallest: y1, z1 (m x nev)
-    for (int e = tid; e < m * m; e += blockDim.x) S.A[e] = H[(e / m) * ldh + (e % m)];
-    __syncthreads();
-    fail |= eig_block(S.A, S.Q, m, m, nev, Wk.lamtmp, Wk.y1, Wk.z1, nev, Wk.W1, Wk.W2, S.v, S.sh, S.ord);
-    // 2. eig(H^(m-1)), nev smallest, padded with a zero row: y2, z2 (m x nev)
-    const int m1 = m - 1;
-    for (int e = tid; e < m1 * m1; e += blockDim.x) S.A[e] = H[(e / m1) * ldh + (e % m1)];
-    __syncthreads();
-    fail |= eig_block(S.A, S.Q, m1, m1, nev, Wk.lamtmp, Wk.y2, Wk.z2, nev, Wk.W1, Wk.W2, S.v, S.sh, S.ord);
-    for (int i = tid; i < nev; i += blockDim.x) { Wk.y2[m1 * nev + i] = czero(); Wk.z2[m1 * nev + i] = czero(); }
-    __syncthreads();
     // 3. y2 -= y1 (z1^H y2), z2 -= z1 (y1^H z2)   (coefficients in S.A as scratch)
     double2* G1 = S.A;                 // nev x nev : z1^H y2
     double2* G2 = S.A + nev * nev;     // nev x nev : y1^H z2
@@ -408,10 +419,10 @@ __device__ int restart_coeffs_block(const double2* H, int ldh, int m, int nev, d
             double best = -1.0; int pr = i, pc = i;
             for (int r = i; r < nev; ++r)
                 for (int c = i; c < nev; ++c) {
-                    double v = cabs_(a[r * nev + c]);
+                    double v = cabs2(a[r * nev + c]);
                     if (v > best) { best = v; pr = r; pc = c; }
                 }
-            if (best < 1e-10) break;
+            if (best < 1e-20) break;   // |pivot| < 1e-10
             if (pr != i) {
                 for (int c = 0; c < nev; ++c) { double2 t = a[i * nev + c]; a[i * nev + c] = a[pr * nev + c]; a[pr * nev + c] = t; }
                 int t = Wk.rowp[i]; Wk.rowp[i] = Wk.rowp[pr]; Wk.rowp[pr] = t;
@@ -492,14 +503,31 @@ __global__ void __launch_bounds__(ET) restart_single_kernel(int m, int nev, cons
     extern __shared__ __align__(16) char smem[];
     EigSmem S(smem, m);
     RestartWork Wk(work, m, nev);
-    int fail = 0;
-    int r = restart_coeffs_block(H, m, m, nev, Yc, Zc, 2 * nev, lam, S, Wk, &fail);
-    if (threadIdx.x == 0) { *r_out = r; *info = fail; }
+    int fail = restart_eigs_part(H, m, m, nev, 0, S, Wk);
+    fail |= restart_eigs_part(H, m, m, nev, 1, S, Wk);
+    int f2 = 0;
+    int r = restart_finish_part(H, m, m, nev, Yc, Zc, 2 * nev, lam, S, Wk, &f2);
+    if (threadIdx.x == 0) { *r_out = r; *info = fail | f2; }
 }
 
-// Restart of every slot whose window is full (vs == m): coefficients, H = diag(lam).
+// Restart of every slot whose window is full (vs == m), in two kernels: the two
+// eigen-solves (one CTA each, grid (nslots, 2)), then the rest (one CTA per
+// slot): coefficients and H = diag(lam).
+__global__ void __launch_bounds__(ET) restart_eigs_kernel(SlotState* states, const SlotPtrs* ptrs,
+                                                          double2* work_base, size_t work_stride, int* fails) {
+    const SlotState& st = states[blockIdx.x];
+    const SlotPtrs& P = ptrs[blockIdx.x];
+    if (!(st.status == ST_RUNNING && st.m > 0 && st.vs == st.m)) return;
+    extern __shared__ __align__(16) char smem[];
+    const int m = st.m, nev = st.nev;
+    EigSmem S(smem, m);
+    RestartWork Wk(work_base + work_stride * blockIdx.x, m, nev);
+    int fail = restart_eigs_part(P.H, m, m, nev, blockIdx.y, S, Wk);
+    if (threadIdx.x == 0) fails[2 * blockIdx.x + blockIdx.y] = fail;
+}
+
 __global__ void __launch_bounds__(ET) restart_slots_kernel(SlotState* states, const SlotPtrs* ptrs,
-                                                           double2* work_base, size_t work_stride) {
+                                                           double2* work_base, size_t work_stride, const int* fails) {
     SlotState& st = states[blockIdx.x];
     const SlotPtrs& P = ptrs[blockIdx.x];
     __shared__ int go;
@@ -515,7 +543,8 @@ __global__ void __launch_bounds__(ET) restart_slots_kernel(SlotState* states, co
     RestartWork Wk(work_base + work_stride * blockIdx.x, m, nev);
     const int ldc = 2 * nev + 1;
     int fail = 0;
-    int r = restart_coeffs_block(P.H, m, m, nev, P.coefY, P.coefZ, ldc, P.lam, S, Wk, &fail);
+    int r = restart_finish_part(P.H, m, m, nev, P.coefY, P.coefZ, ldc, P.lam, S, Wk, &fail);
+    fail |= fails[2 * blockIdx.x] | fails[2 * blockIdx.x + 1];
     // H = diag(lam)
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e % m;
@@ -561,7 +590,7 @@ __global__ void lu_factor_kernel(int n, double2* A, int lda, int* piv, int* info
     for (int k = 0; k < n; ++k) {
         if (threadIdx.x == 0) {
             int p = k; double best = -1.0;
-            for (int i = k; i < n; ++i) { double v = cabs_(A[i * lda + k]); if (v > best) { best = v; p = i; } }
+            for (int i = k; i < n; ++i) { double v = cabs2(A[i * lda + k]); if (v > best) { best = v; p = i; } }
             s_p = p; piv[k] = p;
             if (best == 0.0) s_bad = 1;
         }
@@ -650,6 +679,7 @@ cudaError_t prepare_eig_kernels() {
     if ((e = set_smem((const void*)small_eig_kernel, EigSmem::bytes(MAX_SMALL))) != cudaSuccess) return e;
     if ((e = set_smem((const void*)restart_single_kernel, EigSmem::bytes(MAX_M))) != cudaSuccess) return e;
     if ((e = set_smem((const void*)restart_slots_kernel, EigSmem::bytes(MAX_M))) != cudaSuccess) return e;
+    if ((e = set_smem((const void*)restart_eigs_kernel, EigSmem::bytes(MAX_M))) != cudaSuccess) return e;
     return set_smem((const void*)final_ritz_kernel, EigSmem::bytes(MAX_M));
 }
 
@@ -683,12 +713,15 @@ cudaError_t launch_restart_coeffs_single(int m, int nev, const double2* H, int* 
 
 cudaError_t launch_restart_coeffs(SlotState* states, const SlotPtrs* ptrs, int nslots, double2* w,
                                   cudaStream_t st) {
-    // Per-slot work stride: capacity for the largest window.
-    // (dynamic shared memory opt-in done once by prepare_eig_kernels: this launcher runs under graph capture)
+    // Per-slot work stride: capacity for the largest window; the dynamic shared
+    // memory opt-in is done once by prepare_eig_kernels (this launcher runs under
+    // graph capture).
     const size_t stride = eig_work_elems();
+    int* fails = reinterpret_cast<int*>(w + stride * MAX_SLOTS);   // 2 ints per slot after the slot work areas
     size_t sm = EigSmem::bytes(MAX_M);
-    restart_slots_kernel<<<nslots, ET, sm, st>>>(states, ptrs, w, stride);
-    count_launches(1);
+    restart_eigs_kernel<<<dim3(nslots, 2), ET, sm, st>>>(states, ptrs, w, stride, fails);
+    restart_slots_kernel<<<nslots, ET, sm, st>>>(states, ptrs, w, stride, fails);
+    count_launches(2);
     return cudaGetLastError();
 }
 

@@ -91,17 +91,20 @@ __global__ void convert_kernel(const void* src, void* dst, size_t n) {
 // ------------------------------------------------------------- multidot
 // C[i][j] = sum_e conj(X_i(e)) Y_j(e) for i in [i0, i0+TI), j < b <= BMAX.
 constexpr int MD_TI = 4, MD_BMAX = 8;
+// Grid: (element chunk x column group) flattened with the column group fastest,
+// so the groups that read the same Y chunk run together (Y leaves DRAM once).
 template <typename SX, typename SY, typename T>
 __global__ void __launch_bounds__(BL_THREADS) multidot_kernel(int a, const void* X, int b, const void* Y, size_t N,
-                                                              double2* scratch) {
+                                                              double2* scratch, int nby) {
     using C = cplx<T>;
-    const int i0 = blockIdx.y * MD_TI;
+    const int by = blockIdx.x % nby, bx = blockIdx.x / nby, nbx = gridDim.x / nby;
+    const int i0 = by * MD_TI;
     C acc[MD_TI][MD_BMAX];
 #pragma unroll
     for (int i = 0; i < MD_TI; ++i)
 #pragma unroll
         for (int j = 0; j < MD_BMAX; ++j) acc[i][j] = mk<T>(T(0), T(0));
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = bx * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)nbx * blockDim.x) {
         C y[MD_BMAX];
 #pragma unroll
         for (int j = 0; j < MD_BMAX; ++j)
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(BL_THREADS) multidot_kernel(int a, const void*
     __shared__ double2 sm[(BL_THREADS / 32) * MD_TI * MD_BMAX];
     block_sum<MD_TI * MD_BMAX>(v, sm);
     if (threadIdx.x == 0) {
-        double2* out = scratch + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (MD_TI * MD_BMAX);
+        double2* out = scratch + ((size_t)by * nbx + bx) * (MD_TI * MD_BMAX);
 #pragma unroll
         for (int q = 0; q < MD_TI * MD_BMAX; ++q) out[q] = v[q];
     }
@@ -566,8 +569,18 @@ __global__ void fold_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
 //   V side: H[r][k] = (||r_{j-1}|| / rho_{j-1}) (A^+ phat - conj(beta_{j-2}) s)^H v_k
 //   W side: H[k][r] = (1 / ||r_{j-1}||) w_k^H (A p - beta_{j-2} q)
 // where q, s are the products of the previous iteration (Algorithm eigBiCG).
+//
+// Register tiling: a block covers tiles of WG_E * WG_T elements; each of the
+// RMAX / WG_K column groups computes WG_K output columns for WG_E elements per
+// thread, so one shared-memory coefficient read serves WG_E elements. All
+// groups read a tile's inputs before any group overwrites them (one block
+// barrier per tile: the product is in place).
+constexpr int WG_E = 4, WG_K = 8, WG_T = 64;
+
 template <typename S, int RMAX>
-__global__ void __launch_bounds__(BL_THREADS) window_gemm_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+__global__ void __launch_bounds__(WG_T * ((RMAX + WG_K - 1) / WG_K))
+    window_gemm_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    constexpr int G = (RMAX + WG_K - 1) / WG_K;
     const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
     SlotState& st = states[slot];
     const SlotPtrs& P = ptrs[slot];
@@ -575,47 +588,90 @@ __global__ void __launch_bounds__(BL_THREADS) window_gemm_kernel(SlotState* stat
     using C = cplx<S>;
     const int m = st.m, r = st.restart_r, ldc = 2 * st.nev + 1;
     const int par = st.iter & 1;
-    __shared__ C Cs[(MAX_M + 1) * RMAX];
+    __shared__ C Cs[MAX_M * RMAX];
     const double2* coef = side ? P.coefZ : P.coefY;
-    for (int q = threadIdx.x; q < m * r; q += blockDim.x) {
-        const int i = q / r, k = q % r;
-        double2 sc = side ? P.wscale[i] : make_double2(P.vscale[i], 0.0);
-        Cs[i * RMAX + k] = cvt<S>(sc * coef[i * ldc + k]);
+    for (int q = threadIdx.x; q < m * RMAX; q += blockDim.x) {
+        const int i = q / RMAX, k = q % RMAX;
+        double2 v = make_double2(0.0, 0.0);
+        if (k < r) {
+            double2 sc = side ? P.wscale[i] : make_double2(P.vscale[i], 0.0);
+            v = sc * coef[i * ldc + k];
+        }
+        Cs[q] = cvt<S>(v);
     }
     __syncthreads();
+    const int g = threadIdx.x / WG_T, t = threadIdx.x % WG_T, k0 = g * WG_K;
     // coupling vector: V side c = A^+phat - conj(beta) s ; W side a = A p - beta q
     const C bp = cvt<S>(side ? st.beta_prev : conj_(st.beta_prev));
     const void* cur = side ? P.Ap[par] : P.Ahp[par];
     const void* prv = side ? P.Ap[par ^ 1] : P.Ahp[par ^ 1];
     void* base = side ? P.W : P.V;
-    C dot[RMAX];
+    C dot[WG_K];
 #pragma unroll
-    for (int k = 0; k < RMAX; ++k) dot[k] = mk<S>(S(0), S(0));
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
-        C out[RMAX];
+    for (int kk = 0; kk < WG_K; ++kk) dot[kk] = mk<S>(S(0), S(0));
+    const size_t tile = (size_t)WG_E * WG_T;
+    for (size_t e0 = (size_t)blockIdx.x * tile; e0 < N; e0 += (size_t)gridDim.x * tile) {
+        const size_t eb = e0 + (size_t)t * WG_E;
+        const int ne = eb >= N ? 0 : (int)min((size_t)WG_E, N - eb);
+        C out[WG_E][WG_K];
 #pragma unroll
-        for (int k = 0; k < RMAX; ++k) out[k] = mk<S>(S(0), S(0));
+        for (int e = 0; e < WG_E; ++e)
+#pragma unroll
+            for (int kk = 0; kk < WG_K; ++kk) out[e][kk] = mk<S>(S(0), S(0));
         for (int i = 0; i < m; ++i) {
-            const C x = ld_elem<S>(slot_field<S>(base, i, N), e);
+            const C* src = reinterpret_cast<const C*>(slot_field<S>(base, i, N)) + eb;
+            C x[WG_E];
 #pragma unroll
-            for (int k = 0; k < RMAX; ++k)
-                if (k < r) out[k] = out[k] + x * Cs[i * RMAX + k];
-        }
-        const C last = ld_elem<S>(slot_field<S>(base, m, N), e);
-        const C cv = ld_elem<S>(cur, e) - bp * ld_elem<S>(prv, e);
+            for (int e = 0; e < WG_E; ++e) x[e] = e < ne ? src[e] : mk<S>(S(0), S(0));
 #pragma unroll
-        for (int k = 0; k < RMAX; ++k)
-            if (k < r) {
-                st_elem<S>(slot_field<S>(base, k, N), e, out[k]);
-                dot[k] = dot[k] + (side ? cdot(out[k], cv) : cdot(cv, out[k]));
+            for (int kk = 0; kk < WG_K; ++kk) {
+                const C c = Cs[i * RMAX + k0 + kk];
+#pragma unroll
+                for (int e = 0; e < WG_E; ++e) out[e][kk] = out[e][kk] + x[e] * c;
             }
-        st_elem<S>(slot_field<S>(base, r, N), e, last);
-    }
-    double2 v[RMAX];
+        }
+        C last[WG_E], cv[WG_E];
+        {
+            const C* lsrc = reinterpret_cast<const C*>(slot_field<S>(base, m, N)) + eb;
+            const C* cs = reinterpret_cast<const C*>(cur) + eb;
+            const C* ps = reinterpret_cast<const C*>(prv) + eb;
 #pragma unroll
-    for (int k = 0; k < RMAX; ++k) v[k] = to_d(dot[k]);
-    double2 tot[RMAX];
-    if (reduce_slot<RMAX>(P, side ? CNT_GEMM_W : CNT_GEMM_V, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+            for (int e = 0; e < WG_E; ++e) {
+                last[e] = (g == 0 && e < ne) ? lsrc[e] : mk<S>(S(0), S(0));
+                cv[e] = e < ne ? cs[e] - bp * ps[e] : mk<S>(S(0), S(0));
+            }
+        }
+        __syncthreads();   // every group has read this tile's inputs
+#pragma unroll
+        for (int kk = 0; kk < WG_K; ++kk) {
+            const int k = k0 + kk;
+            if (k < r) {
+                C* dst = reinterpret_cast<C*>(slot_field<S>(base, k, N)) + eb;
+#pragma unroll
+                for (int e = 0; e < WG_E; ++e)
+                    if (e < ne) {
+                        dst[e] = out[e][kk];
+                        dot[kk] = dot[kk] + (side ? cdot(out[e][kk], cv[e]) : cdot(cv[e], out[e][kk]));
+                    }
+            }
+        }
+        if (g == 0) {
+            C* dst = reinterpret_cast<C*>(slot_field<S>(base, r, N)) + eb;
+#pragma unroll
+            for (int e = 0; e < WG_E; ++e)
+                if (e < ne) dst[e] = last[e];
+        }
+    }
+    double2 v[G * WG_K];
+#pragma unroll
+    for (int q = 0; q < G * WG_K; ++q) v[q] = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg)
+        if (gg == g)
+#pragma unroll
+            for (int kk = 0; kk < WG_K; ++kk) v[gg * WG_K + kk] = to_d(dot[kk]);
+    double2 tot[G * WG_K];
+    if (reduce_slot<G * WG_K>(P, side ? CNT_GEMM_W : CNT_GEMM_V, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
         // the new basis vectors are stored normalised: their window scale is 1
         if (side) {
             const double f = 1.0 / st.rnorm;
@@ -686,11 +742,11 @@ cudaError_t launch_multidot(int a, const void* X, int xp, int b, const void* Y, 
         while ((size_t)nbx * nby * MD_TI * MD_BMAX > scratch_elems && nbx > 1) nbx /= 2;
         if ((size_t)nbx * nby * MD_TI * MD_BMAX > scratch_elems) return cudaErrorInvalidValue;
         const char* Yj = reinterpret_cast<const char*>(Y) + (size_t)j0 * N * (yp == 0 ? 16 : 8);
-        dim3 grid(nbx, nby);
-        if (xp == 1 && yp == 1) multidot_kernel<float, float, float><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
-        else if (xp == 1 && yp == 0) multidot_kernel<float, double, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
-        else if (xp == 0 && yp == 1) multidot_kernel<double, float, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
-        else multidot_kernel<double, double, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch);
+        const int grid = nbx * nby;
+        if (xp == 1 && yp == 1) multidot_kernel<float, float, float><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch, nby);
+        else if (xp == 1 && yp == 0) multidot_kernel<float, double, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch, nby);
+        else if (xp == 0 && yp == 1) multidot_kernel<double, float, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch, nby);
+        else multidot_kernel<double, double, double><<<grid, BL_THREADS, 0, st>>>(a, X, bb, Yj, N, scratch, nby);
         count_launches(2);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -826,26 +882,23 @@ cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa,
     return cudaGetLastError();
 }
 
+template <typename S, int RMAX>
+static void window_gemm_launch(SlotState* states, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s) {
+    constexpr int threads = WG_T * ((RMAX + WG_K - 1) / WG_K);
+    int nb = div_up(N, (size_t)WG_E * WG_T);
+    if (nb > 2 * 152) nb = 2 * 152;
+    if (nb > PARTIAL_STRIDE / RMAX) nb = PARTIAL_STRIDE / RMAX;
+    window_gemm_kernel<S, RMAX><<<dim3(nb, 2 * nslots), threads, 0, s>>>(states, ptrs, N);
+}
+
 template <typename S>
 static cudaError_t window_gemm_dispatch(int rmax_needed, SlotState* states, const SlotPtrs* ptrs, int nslots,
                                         size_t N, cudaStream_t s) {
-    int nb = blas_blocks(N);
-    dim3 grid(nb, 2 * nslots);
-    if (rmax_needed <= 8) {
-        grid.x = nb < PARTIAL_STRIDE / 8 ? nb : PARTIAL_STRIDE / 8;
-        window_gemm_kernel<S, 8><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
-    } else if (rmax_needed <= 16) {
-        grid.x = nb < PARTIAL_STRIDE / 16 ? nb : PARTIAL_STRIDE / 16;
-        window_gemm_kernel<S, 16><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
-    } else if (rmax_needed <= 24) {
-        grid.x = nb < PARTIAL_STRIDE / 24 ? nb : PARTIAL_STRIDE / 24;
-        window_gemm_kernel<S, 24><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
-    } else if (rmax_needed <= 32) {
-        grid.x = nb < PARTIAL_STRIDE / 32 ? nb : PARTIAL_STRIDE / 32;
-        window_gemm_kernel<S, 32><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
-    } else {
-        return cudaErrorInvalidValue;
-    }
+    if (rmax_needed <= 8) window_gemm_launch<S, 8>(states, ptrs, nslots, N, s);
+    else if (rmax_needed <= 16) window_gemm_launch<S, 16>(states, ptrs, nslots, N, s);
+    else if (rmax_needed <= 24) window_gemm_launch<S, 24>(states, ptrs, nslots, N, s);
+    else if (rmax_needed <= 32) window_gemm_launch<S, 32>(states, ptrs, nslots, N, s);
+    else return cudaErrorInvalidValue;
     count_launches(1);
     return cudaGetLastError();
 }

@@ -76,7 +76,8 @@ cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa,
                                SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
 
 // eigBiCG restart: coefficient kernel (one CTA per slot) and window product.
-// Work buffers: eig_work_elems() double2 per slot (restart) or per call (the others).
+// Work buffers: eig_work_elems() double2 per slot (restart; the buffer holds MAX_SLOTS
+// slot areas plus 16 double2 for status words) or per call (the others).
 size_t eig_work_elems();
 // Opt the eigen kernels into large dynamic shared memory (call once, outside graph capture).
 cudaError_t prepare_eig_kernels();

@@ -248,7 +248,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     size_t plan = (size_t)c->V * 4 * 9 * 16 + (c->kprec ? (size_t)c->V * 4 * 3 * 16 : 0);
     plan += K * c->kbytes * (1 + 2 * (c->m + 1) + 6) + K * c->dbytes * 4;
     plan += 2 * (size_t)c->n_def_max * c->kbytes;
-    plan += K * eig_work_elems() * 16 + c->mdscratch_elems * 16 + K * CNT_COUNT * PARTIAL_STRIDE * 16;
+    plan += (MAX_SLOTS * eig_work_elems() + 16) * 16 + c->mdscratch_elems * 16 + K * CNT_COUNT * PARTIAL_STRIDE * 16;
     if (c->p.hbm_budget_bytes && plan > c->p.hbm_budget_bytes) {
         g_last_error = "memory plan exceeds hbm_budget_bytes";
         delete c;
@@ -285,7 +285,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     AL(c->small_all, K * c->small_stride * 16);
     AL(c->partials, K * CNT_COUNT * PARTIAL_STRIDE * 16);
     AL(c->counters, K * CNT_COUNT * sizeof(unsigned));
-    AL(c->eigwork, K * eig_work_elems() * 16);
+    AL(c->eigwork, ((size_t)MAX_SLOTS * eig_work_elems() + 16) * 16);
     AL(c->mdscratch, c->mdscratch_elems * 16);
     AL(c->d_jobs, sizeof(ApplyJob) * 2 * K);
     AL(c->staging, K * c->dbytes);
