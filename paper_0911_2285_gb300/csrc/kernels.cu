@@ -182,6 +182,27 @@ __global__ void __launch_bounds__(BL_THREADS) vupdate_kernel(int a, const void* 
     }
 }
 
+// Per-field squared 2-norms of b fields: block partials (FP64) for a second pass.
+template <typename S>
+__global__ void __launch_bounds__(BL_THREADS) norms_kernel(const void* Y, size_t N, double2* scratch) {
+    const int j = blockIdx.y;
+    const cplx<S>* y = reinterpret_cast<const cplx<S>*>(Y) + (size_t)j * N;
+    S acc = S(0);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x)
+        acc += abs2(y[e]);
+    double2 v[1] = {make_double2((double)acc, 0.0)};
+    __shared__ double2 sm[BL_THREADS / 32];
+    block_sum<1>(v, sm);
+    if (threadIdx.x == 0) scratch[(size_t)j * gridDim.x + blockIdx.x] = v[0];
+}
+__global__ void norms_reduce_kernel(int b, int nb, const double2* scratch, double* out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= b) return;
+    double acc = 0.0;
+    for (int i = 0; i < nb; ++i) acc += scratch[(size_t)j * nb + i].x;
+    out[j] = sqrt(acc);
+}
+
 // Y_j *= s_j (per-field scale), j < b.
 template <typename S>
 __global__ void scale_fields_kernel(int b, void* Y, const double2* sc, size_t N) {
@@ -618,17 +639,27 @@ __global__ void __launch_bounds__(WG_T * ((RMAX + WG_K - 1) / WG_K))
         for (int e = 0; e < WG_E; ++e)
 #pragma unroll
             for (int kk = 0; kk < WG_K; ++kk) out[e][kk] = mk<S>(S(0), S(0));
-        for (int i = 0; i < m; ++i) {
-            const C* src = reinterpret_cast<const C*>(slot_field<S>(base, i, N)) + eb;
-            C x[WG_E];
+        // inputs of slot i+1 are loaded while slot i is multiplied (software pipelining)
+        C x[WG_E], xn[WG_E];
+        {
+            const C* src = reinterpret_cast<const C*>(base) + eb;
 #pragma unroll
             for (int e = 0; e < WG_E; ++e) x[e] = e < ne ? src[e] : mk<S>(S(0), S(0));
+        }
+        for (int i = 0; i < m; ++i) {
+            if (i + 1 < m) {
+                const C* src = reinterpret_cast<const C*>(slot_field<S>(base, i + 1, N)) + eb;
+#pragma unroll
+                for (int e = 0; e < WG_E; ++e) xn[e] = e < ne ? src[e] : mk<S>(S(0), S(0));
+            }
 #pragma unroll
             for (int kk = 0; kk < WG_K; ++kk) {
                 const C c = Cs[i * RMAX + k0 + kk];
 #pragma unroll
                 for (int e = 0; e < WG_E; ++e) out[e][kk] = out[e][kk] + x[e] * c;
             }
+#pragma unroll
+            for (int e = 0; e < WG_E; ++e) x[e] = xn[e];
         }
         C last[WG_E], cv[WG_E];
         {
@@ -662,23 +693,44 @@ __global__ void __launch_bounds__(WG_T * ((RMAX + WG_K - 1) / WG_K))
                 if (e < ne) dst[e] = last[e];
         }
     }
-    double2 v[G * WG_K];
+    // block sums of the coupling dots: warp shuffles, then one value per thread
+    __shared__ double2 wdot[(WG_T * G / 32) * WG_K];
+    __shared__ bool am_last;
 #pragma unroll
-    for (int q = 0; q < G * WG_K; ++q) v[q] = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int gg = 0; gg < G; ++gg)
-        if (gg == g)
-#pragma unroll
-            for (int kk = 0; kk < WG_K; ++kk) v[gg * WG_K + kk] = to_d(dot[kk]);
-    double2 tot[G * WG_K];
-    if (reduce_slot<G * WG_K>(P, side ? CNT_GEMM_W : CNT_GEMM_V, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+    for (int kk = 0; kk < WG_K; ++kk) {
+        double2 d = warp_sum(to_d(dot[kk]));
+        if ((threadIdx.x & 31) == 0) wdot[(threadIdx.x >> 5) * WG_K + kk] = d;
+    }
+    __syncthreads();
+    constexpr int WPG = WG_T / 32;   // warps per column group
+    double2* pp = P.partials + (size_t)(side ? CNT_GEMM_W : CNT_GEMM_V) * PARTIAL_STRIDE;
+    const int q = threadIdx.x;       // output column q = group * WG_K + kk
+    if (q < G * WG_K) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int w = 0; w < WPG; ++w) acc = acc + wdot[((q / WG_K) * WPG + w) * WG_K + q % WG_K];
+        pp[(size_t)blockIdx.x * (G * WG_K) + q] = acc;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(P.counters + (side ? CNT_GEMM_W : CNT_GEMM_V), 1u);
+        am_last = (prev == gridDim.x - 1);
+        if (am_last) P.counters[side ? CNT_GEMM_W : CNT_GEMM_V] = 0;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    if (q < r) {
+        // the last block adds the partials in block order (deterministic)
+        double2 tot = make_double2(0.0, 0.0);
+        for (unsigned b = 0; b < gridDim.x; ++b) tot = tot + __ldcg(pp + (size_t)b * (G * WG_K) + q);
         // the new basis vectors are stored normalised: their window scale is 1
         if (side) {
-            const double f = 1.0 / st.rnorm;
-            for (int k = 0; k < r; ++k) { P.H[k * m + r] = f * tot[k]; P.wscale[k] = make_double2(1.0, 0.0); }
+            P.H[q * m + r] = (1.0 / st.rnorm) * tot;
+            P.wscale[q] = make_double2(1.0, 0.0);
         } else {
-            const double2 f = cdiv(make_double2(st.rnorm, 0.0), st.rho);
-            for (int k = 0; k < r; ++k) { P.H[r * m + k] = f * tot[k]; P.vscale[k] = 1.0; }
+            P.H[r * m + q] = cdiv(make_double2(st.rnorm, 0.0), st.rho) * tot;
+            P.vscale[q] = 1.0;
         }
     }
 }
@@ -775,6 +827,20 @@ cudaError_t launch_vupdate(int a, const void* X, int xp, const double2* D, int l
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_norms(int b, const void* Y, int yp, size_t N, double* out, double2* scratch,
+                         size_t scratch_elems, cudaStream_t st) {
+    if (b <= 0) return cudaSuccess;
+    int nb = blas_blocks(N) / 2;
+    if (nb < 1) nb = 1;
+    while ((size_t)nb * b > scratch_elems && nb > 1) nb /= 2;
+    dim3 grid(nb, b);
+    if (yp == 0) norms_kernel<double><<<grid, BL_THREADS, 0, st>>>(Y, N, scratch);
+    else norms_kernel<float><<<grid, BL_THREADS, 0, st>>>(Y, N, scratch);
+    norms_reduce_kernel<<<(b + 63) / 64, 64, 0, st>>>(b, nb, scratch, out);
+    count_launches(2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_scale_fields(int b, void* Y, int yp, const double2* sc, size_t N, cudaStream_t st) {

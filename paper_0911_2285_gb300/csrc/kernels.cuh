@@ -44,6 +44,9 @@ cudaError_t launch_multidot(int a, const void* X, int xprec, int b, const void* 
 // The arithmetic is FP32 when X is FP32 (the sum is added to an FP64 Y in FP64).
 cudaError_t launch_vupdate(int a, const void* X, int xprec, const double2* D, int ldd, int b,
                            void* Y, int yprec, int overwrite, size_t N, cudaStream_t st);
+// out[j] = ||Y_j|| (FP64 result, device) for b fields.
+cudaError_t launch_norms(int b, const void* Y, int yprec, size_t N, double* out, double2* scratch,
+                         size_t scratch_elems, cudaStream_t st);
 // Y_j *= sc[j] for b fields (sc on the device).
 cudaError_t launch_scale_fields(int b, void* Y, int yprec, const double2* sc, size_t N, cudaStream_t st);
 

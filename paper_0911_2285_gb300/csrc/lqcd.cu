@@ -495,8 +495,8 @@ lqcd_status refactor(lqcd_ctx* c) {
 // Append nn new pairs (already stored at columns n_def.. of Ur/Ul) after
 // bi-orthogonalizing them against the existing space (Algorithm Incremental,
 // step 2), scaling to unit norm and growing H = U_l^H A U_r and M = U_l^H U_r.
-// work: at least 2*nn FP64 fields.
-lqcd_status grow_space(lqcd_ctx* c, int nn, double2* work) {
+// work: at least 4*nn Krylov fields (A V', V', A^H W', W').
+lqcd_status grow_space(lqcd_ctx* c, int nn, void* work) {
     const int n = c->n_def, ld = c->n_def_max;
     nn = std::min(nn, c->n_def_max - n);
     if (nn <= 0) return LQCD_OK;
@@ -505,15 +505,13 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, double2* work) {
     const int kp = c->kprec;
     double2* G = c->dsmall;                        // n x nn
     double2* G2 = G + (size_t)MAX_SMALL * 16;      // n x nn
-    double2* NV0 = G2 + (size_t)MAX_SMALL * 16;    // nn x nn gram (before)
-    double2* NW0 = NV0 + 256;
-    double2* NV1 = NW0 + 256;
-    double2* NW1 = NV1 + 256;
-    double2* sc = NW1 + 256;                       // nn scales (V), nn (W)
+    double2* T1 = G2 + (size_t)MAX_SMALL * 16;     // (n+nn) x 2nn
+    double2* T2 = T1 + (size_t)MAX_SMALL * 32;     // n x 2nn (conjugate-transposed store: 2nn x n)
+    double2* sc = T2 + (size_t)MAX_SMALL * 32;     // nn scales (V), nn (W)
     double* nrm = reinterpret_cast<double*>(sc + 64);   // 4*nn doubles
     // norms before the projection
-    CK(launch_multidot(nn, Vn, kp, nn, Vn, kp, c->N, NV0, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
-    CK(launch_multidot(nn, Wn, kp, nn, Wn, kp, c->N, NW0, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_norms(nn, Vn, kp, c->N, nrm, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_norms(nn, Wn, kp, c->N, nrm + nn, c->mdscratch, c->mdscratch_elems, c->stream));
     if (n > 0) {
         // V' = V - U_r M^{-1} U_l^H V ;  W' = W - U_l M^{-H} U_r^H W
         CK(launch_multidot(n, c->Ul, kp, nn, Vn, kp, c->N, G, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
@@ -527,24 +525,22 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, double2* work) {
         CK(launch_vupdate(n, c->Ur, kp, G, nn, nn, Vn, kp, 0, c->N, c->stream));
         CK(launch_vupdate(n, c->Ul, kp, G2, nn, nn, Wn, kp, 0, c->N, c->stream));
     }
-    CK(launch_multidot(nn, Vn, kp, nn, Vn, kp, c->N, NV1, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
-    CK(launch_multidot(nn, Wn, kp, nn, Wn, kp, c->N, NW1, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
-    inv_norm_kernel<<<1, 64, 0, c->stream>>>(NV0, nn, nn, sc + 32, nrm);
-    inv_norm_kernel<<<1, 64, 0, c->stream>>>(NW0, nn, nn, sc + 32, nrm + nn);
-    inv_norm_kernel<<<1, 64, 0, c->stream>>>(NV1, nn, nn, sc, nrm + 2 * nn);
-    inv_norm_kernel<<<1, 64, 0, c->stream>>>(NW1, nn, nn, sc + nn, nrm + 3 * nn);
-    count_launches(4);
-    CK(cudaGetLastError());
+    CK(launch_norms(nn, Vn, kp, c->N, nrm + 2 * nn, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_norms(nn, Wn, kp, c->N, nrm + 3 * nn, c->mdscratch, c->mdscratch_elems, c->stream));
     std::vector<double> hn(4 * nn);
     CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * 4 * nn, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     // keep pairs whose projected columns retain more than 1e-8 of their norm
     std::vector<int> keep;
+    std::vector<double2> hsc(2 * nn, make_double2(0.0, 0.0));
     for (int i = 0; i < nn; ++i) {
         const double nv0 = hn[i], nw0 = hn[nn + i], nv = hn[2 * nn + i], nw = hn[3 * nn + i];
         if (nv > 1e-8 * nv0 && nw > 1e-8 * nw0 && std::isfinite(nv) && std::isfinite(nw)) keep.push_back(i);
+        hsc[i] = make_double2(nv > 0 ? 1.0 / nv : 0.0, 0.0);
+        hsc[nn + i] = make_double2(nw > 0 ? 1.0 / nw : 0.0, 0.0);
     }
-    // scale to unit norm (device scales), then compact the kept columns
+    CK(cudaMemcpyAsync(sc, hsc.data(), sizeof(double2) * 2 * nn, cudaMemcpyHostToDevice, c->stream));
+    // scale to unit norm, then compact the kept columns
     CK(launch_scale_fields(nn, Vn, kp, sc, c->N, c->stream));
     CK(launch_scale_fields(nn, Wn, kp, sc + nn, c->N, c->stream));
     int kk = 0;
@@ -556,53 +552,32 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, double2* work) {
         ++kk;
     }
     if (kk == 0) return LQCD_OK;
-    // A V' and A^H W' in FP64 (upcast FP32 columns first)
-    double2* AV = work;
-    double2* AW = work + (size_t)kk * c->N;
-    const void* Vin = Vn;
-    const void* Win = Wn;
-    if (kp) {
-        // FP32 columns: upcast into AV / AW, which are then overwritten column by column
-        CK(launch_convert(Vn, 1, AV, 0, (size_t)kk * c->N, c->stream));
-        CK(launch_convert(Wn, 1, AW, 0, (size_t)kk * c->N, c->stream));
-        Vin = AV;
-        Win = AW;
-    }
-    // apply in place is not allowed (stencil reads neighbours): go through staging in chunks
-    for (int j = 0; j < kk; ++j) {
-        lqcd_status s = apply_fields(c, 0, 0, 1, reinterpret_cast<const char*>(Vin) + (size_t)j * (kp ? c->dbytes : c->kbytes),
-                                     0, c->staging, 0, nullptr);
-        if (s != LQCD_OK) return s;
-        CK(cudaMemcpyAsync(AV + (size_t)j * c->N, c->staging, c->dbytes, cudaMemcpyDeviceToDevice, c->stream));
-        s = apply_fields(c, 0, 1, 1, reinterpret_cast<const char*>(Win) + (size_t)j * (kp ? c->dbytes : c->kbytes), 0,
-                         c->staging, 0, nullptr);
-        if (s != LQCD_OK) return s;
-        CK(cudaMemcpyAsync(AW + (size_t)j * c->N, c->staging, c->dbytes, cudaMemcpyDeviceToDevice, c->stream));
-    }
-    // blocks of H (ld n_def_max): [H, U_l^H AV'; (A^H W')^H U_r, W'^H AV']
-    // and of M: [M, U_l^H V'; W'^H U_r, W'^H V']. With FP32 storage the
-    // projections run in FP32 on FP32 copies of A V', A^H W' (FP64 sums per block).
-    double2* Hn = c->Hdef;
-    double2* Mn = c->Mdef;
-    const void* AVp = AV;
-    const void* AWp = AW;
-    int ap = 0;
-    if (kp) {
-        char* f32 = reinterpret_cast<char*>(AW + (size_t)kk * c->N);
-        CK(launch_convert(AV, 0, f32, 1, (size_t)kk * c->N, c->stream));
-        CK(launch_convert(AW, 0, f32 + (size_t)kk * c->kbytes, 1, (size_t)kk * c->N, c->stream));
-        AVp = f32;
-        AWp = f32 + (size_t)kk * c->kbytes;
-        ap = 1;
-    }
+    // [A V' | V'] and [A^H W' | W'] side by side in the work area, in the storage
+    // precision (FP32 operator with two-row links for FP32 storage: the
+    // projections are FP32 sums as well, and lqcd_eigs recomputes its pencil in FP64)
+    char* AV = reinterpret_cast<char*>(work);
+    char* AW = AV + (size_t)2 * kk * c->kbytes;
+    lqcd_status s = apply_fields(c, kp, 0, kk, Vn, c->kbytes, AV, c->kbytes, nullptr);
+    if (s != LQCD_OK) return s;
+    s = apply_fields(c, kp, 1, kk, Wn, c->kbytes, AW, c->kbytes, nullptr);
+    if (s != LQCD_OK) return s;
+    CK(cudaMemcpyAsync(AV + (size_t)kk * c->kbytes, Vn, (size_t)kk * c->kbytes, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(AW + (size_t)kk * c->kbytes, Wn, (size_t)kk * c->kbytes, cudaMemcpyDeviceToDevice, c->stream));
+    // [U_l W']^H [A V' | V'] -> H[:, n:n+kk] and M[:, n:n+kk]  (rows 0..n+kk)
+    const int nt = n + kk;
+    CK(launch_multidot(nt, c->Ul, kp, 2 * kk, AV, kp, c->N, T1, 2 * kk, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    copy_block_kernel<<<16, 256, 0, c->stream>>>(T1, 2 * kk, c->Hdef + n, ld, nt, kk);
+    copy_block_kernel<<<16, 256, 0, c->stream>>>(T1 + kk, 2 * kk, c->Mdef + n, ld, nt, kk);
+    count_launches(2);
+    CK(cudaGetLastError());
     if (n > 0) {
-        CK(launch_multidot(n, c->Ul, kp, kk, AVp, ap, c->N, Hn + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
-        CK(launch_multidot(n, c->Ur, kp, kk, AWp, ap, c->N, Hn + (size_t)n * ld, ld, 1, c->mdscratch, c->mdscratch_elems, c->stream));
-        CK(launch_multidot(n, c->Ul, kp, kk, Vn, kp, c->N, Mn + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
-        CK(launch_multidot(n, c->Ur, kp, kk, Wn, kp, c->N, Mn + (size_t)n * ld, ld, 1, c->mdscratch, c->mdscratch_elems, c->stream));
+        // (A^H W')^H U_r -> H[n:n+kk, 0:n] ;  W'^H U_r -> M[n:n+kk, 0:n]
+        CK(launch_multidot(n, c->Ur, kp, 2 * kk, AW, kp, c->N, T2, n, 1, c->mdscratch, c->mdscratch_elems, c->stream));
+        copy_block_kernel<<<16, 256, 0, c->stream>>>(T2, n, c->Hdef + (size_t)n * ld, ld, kk, n);
+        copy_block_kernel<<<16, 256, 0, c->stream>>>(T2 + (size_t)kk * n, n, c->Mdef + (size_t)n * ld, ld, kk, n);
+        count_launches(2);
+        CK(cudaGetLastError());
     }
-    CK(launch_multidot(kk, Wn, kp, kk, AVp, ap, c->N, Hn + (size_t)n * ld + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
-    CK(launch_multidot(kk, Wn, kp, kk, Vn, kp, c->N, Mn + (size_t)n * ld + n, ld, 0, c->mdscratch, c->mdscratch_elems, c->stream));
     c->n_def = n + kk;
     return refactor(c);
 }
@@ -753,9 +728,9 @@ lqcd_status grow_from_windows(lqcd_ctx* c, int k) {
         CK(launch_vupdate(vs, P.W, c->kprec, Zc, nsel, take, c->krylov(c->Ul, c->n_def), c->kprec, 1, c->N, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         c->last_ritz[s] = hl;
-        // work fields for A V', A^H W' (FP64, plus their FP32 copies in MIXED): this
-        // slot's window, which holds 2(m+1) > 4 nev Krylov fields
-        double2* work = reinterpret_cast<double2*>(P.V);
+        // work fields for [A V' | V'], [A^H W' | W']: this slot's window, which
+        // holds 2(m+1) > 4 nev Krylov fields
+        void* work = P.V;
         lqcd_status r = grow_space(c, take, work);
         if (r != LQCD_OK) return r;
         c->eig_rhs_done += 1;
