@@ -207,6 +207,26 @@ int lqcd_dslash_variant(const lqcd_ctx *ctx);
 lqcd_status lqcd_apply_pair(lqcd_ctx *ctx, int variant, int k, const double *p, const double *phat,
                             double *Ap, double *Ahp, double *sigma);
 
+/* Allocation-free eigen-solver (no counterpart in the paper; a service for
+ * callers that cannot allocate device memory when they need a small
+ * eigen-solve: applications that give all device memory to their own pool or
+ * a fixed budget up front, and latency-critical loops where the implicit device
+ * synchronisation of cudaMalloc/cudaFree would stall other streams).
+ * Same results as lqcd_small_eig, but C (n x n complex row-major), evals (n
+ * complex) and Y, Z (n x n, or both NULL for eigenvalues only) are DEVICE
+ * pointers on the current device, and nothing is allocated: the scratch lives
+ * in a file-scope device array sized for n <= 80 (about 200 KiB, held by every
+ * GPU that loads the library until the process exits).  n > 80 returns
+ * LQCD_ERR_ARG.  The first call on a device looks up that array's device
+ * address and sets the kernel's shared-memory limit, so make the first call
+ * before any stream capture.  Work is ordered on 'cuda_stream' (cudaStream_t,
+ * NULL = default stream) and the call returns after it completes.  All calls on
+ * a device share the scratch array and it keeps the last call's contents: calls
+ * whose kernels overlap on the GPU (other streams, other host threads) race.
+ * LQCD_ERR_NOCONV if the QR iteration did not converge. */
+lqcd_status lqcd_small_eig_noalloc(int n, const double *C, double *evals, double *Y, double *Z,
+                                   void *cuda_stream);
+
 /* Text for a status code. */
 const char *lqcd_status_str(lqcd_status s);
 

@@ -11,6 +11,9 @@
 // substitution, mapped back with Q. Conventions: right vectors have unit
 // 2-norm with their largest-modulus entry real positive; left vectors satisfy
 // z^H y = 1.
+#include <mutex>
+
+#include "../../include/lqcd.h"
 #include "kernels.cuh"
 
 namespace lqcd {
@@ -755,4 +758,78 @@ cudaError_t launch_small_gemm(int n, int k, int m, const double2* A, int lda, in
     return cudaGetLastError();
 }
 
+
+// ============================================================================
+// Allocation-free variant of the small eigen-solver (no counterpart in the paper).
+//
+// lqcd_small_eig stages its operands through cudaMalloc'd buffers. Some callers
+// cannot allocate device memory at the point where they need an eigen-solve:
+// host applications that hand all device memory to their own pool or fixed
+// budget up front, and latency-critical loops where the implicit device
+// synchronisation of cudaMalloc/cudaFree would stall work on other streams.
+// lqcd_small_eig_noalloc takes device pointers for the input and every output
+// and keeps its scratch (the substitution vectors and a status word) in the
+// file-scope device array below: at most NOALLOC_MAX_N = 80, i.e. 2*80*80 + 16
+// complex doubles (about 200 KiB), held by every GPU that loads the library
+// until the process exits. The array is shared by all calls on a device and
+// keeps the last call's contents: the status word is cleared by each call, the
+// substitution vectors are fully rewritten before they are read. Calls whose
+// kernels overlap on the GPU (different streams, or host threads) race on it.
+namespace {
+
+constexpr int NOALLOC_MAX_N = MAX_SMALL;
+constexpr size_t NOALLOC_SCRATCH = (size_t)2 * NOALLOC_MAX_N * NOALLOC_MAX_N;
+
+static __device__ __align__(256) double2 g_noalloc_scratch[NOALLOC_SCRATCH + 16];
+
+struct NoAllocSetup {
+    bool ready = false;
+    double2* scratch = nullptr;   // device address of g_noalloc_scratch on this device
+};
+constexpr int NOALLOC_MAX_DEVICES = 64;
+NoAllocSetup g_noalloc_dev[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mutex;
+
+// Once per device, with that device current: the array's device address and the
+// kernel's shared-memory opt-in.
+cudaError_t noalloc_setup(int dev, double2** scratch) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoAllocSetup& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        e = set_smem((const void*)small_eig_kernel, EigSmem::bytes(NOALLOC_MAX_N));
+        if (e != cudaSuccess) return e;
+        d.scratch = reinterpret_cast<double2*>(p);
+        d.ready = true;
+    }
+    *scratch = d.scratch;
+    return cudaSuccess;
+}
+
+}  // namespace
 }  // namespace lqcd
+
+extern "C" lqcd_status lqcd_small_eig_noalloc(int n, const double* C, double* evals, double* Y, double* Z,
+                                              void* stream) {
+    using namespace lqcd;
+    if (n < 1 || n > NOALLOC_MAX_N || !C || !evals || (Y == nullptr) != (Z == nullptr)) return LQCD_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return LQCD_ERR_CUDA;
+    double2* scratch = nullptr;
+    if (noalloc_setup(dev, &scratch) != cudaSuccess) return LQCD_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int* info = reinterpret_cast<int*>(scratch + NOALLOC_SCRATCH);
+    const int nsel = Y ? n : 0;
+    if (cudaMemsetAsync(info, 0, sizeof(int), st) != cudaSuccess) return LQCD_ERR_CUDA;
+    small_eig_kernel<<<1, ET, EigSmem::bytes(n), st>>>(n, reinterpret_cast<const double2*>(C), n, nsel,
+                                                       reinterpret_cast<double2*>(evals), reinterpret_cast<double2*>(Y),
+                                                       reinterpret_cast<double2*>(Z), n, scratch, info);
+    count_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return LQCD_ERR_CUDA;
+    int hinfo = 0;
+    if (cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LQCD_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LQCD_ERR_CUDA;
+    return hinfo ? LQCD_ERR_NOCONV : LQCD_OK;
+}

@@ -98,6 +98,8 @@ def lib():
         L.lqcd_kernel_launches.restype = C.c_longlong
         L.lqcd_time_kernel.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
         L.lqcd_time_kernel.restype = C.c_int
+        L.lqcd_small_eig_noalloc.argtypes = [C.c_int, vp, vp, vp, vp, vp]
+        L.lqcd_small_eig_noalloc.restype = C.c_int
         L.lqcd_apply_pair.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
         L.lqcd_apply_pair.restype = C.c_int
         L.lqcd_dslash_variant.argtypes = [vp]
