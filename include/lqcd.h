@@ -122,11 +122,40 @@ lqcd_status lqcd_eigbicg_init(lqcd_ctx **ctx, const lqcd_params *params,
  * call and append in index order at the end.  DEFLATED: deflate, BiCG, and with
  * deftol > 0 one re-deflation restart at ||r|| < deftol ||b|| (phase 2).
  * info: k entries (may be NULL).  k may exceed k_max: the sources are then
- * processed in batches of k_max (continuous refill of freed slots).
+ * processed in consecutive batches of k_max (for continuous refill of freed
+ * slots use the serving session below).
  * Returns LQCD_ERR_NOCONV / LQCD_ERR_BREAKDOWN if any source failed; x then
  * holds the best iterate. */
 lqcd_status lqcd_solve(lqcd_ctx *ctx, int k, const double *b, double *x,
                        int on_device, lqcd_mode mode, lqcd_solve_info *info);
+
+/* Serving session (continuous batching): requests wait in a queue, take a
+ * batch slot as soon as one frees up and leave it when their solve ends, while
+ * the other slots keep iterating; the gauge field and the eigenspace stay
+ * resident.  The mode is resolved at admission (AUTO: eigBiCG while fewer than
+ * n1 sources have fed or are feeding the eigenspace, deflated BiCG after).
+ * The context must not run lqcd_solve while requests are in flight
+ * (LQCD_ERR_STATE).
+ *
+ * lqcd_submit: queue one right-hand side.  b and x are one field each (host or
+ * device as on_device says); b is read when the request is admitted, x holds
+ * the initial guess until then and receives the solution when it completes:
+ * both must stay valid until lqcd_poll reports it done.  *ticket identifies it. */
+lqcd_status lqcd_submit(lqcd_ctx *ctx, const double *b, double *x, int on_device, lqcd_mode mode,
+                        long long *ticket);
+
+/* Advance the session: wait for the iterations in flight, retire finished
+ * requests (final FP64 residual, eigenspace growth, solution written), admit
+ * queued requests into free slots (deflation, start vectors) and launch the
+ * next chunk of 8 BiCG iterations for every busy slot without waiting for it.
+ * *pending = requests queued or in slots (may be NULL). */
+lqcd_status lqcd_progress(lqcd_ctx *ctx, int *pending);
+
+/* Completion of a submitted request: *done = 1 and *info / *result (the solve's
+ * own status, e.g. LQCD_ERR_NOCONV) once it finished (each reported once);
+ * *done = 0 while it is queued or running.  LQCD_ERR_ARG for an unknown ticket. */
+lqcd_status lqcd_poll(lqcd_ctx *ctx, long long ticket, int *done, lqcd_solve_info *info,
+                      lqcd_status *result);
 
 /* Oblique deflation of k initial guesses (Alg. Incremental, steps 2 and 3):
  * x0 <- x0 + U_r d,  with  H d = U_l^+ (b - A x0),  H = U_l^+ A U_r.

@@ -13,6 +13,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -107,6 +109,41 @@ struct lqcd_ctx {
     // CUDA graphs of CHECK_EVERY iterations, keyed by (nslots, windowed)
     cudaGraphExec_t graphs[MAX_SLOTS + 1][2] = {};
     long long graph_nodes[MAX_SLOTS + 1][2] = {};
+
+    // serving session (lqcd_submit / lqcd_progress / lqcd_poll): requests wait in
+    // a queue, take a batch slot as soon as one is free, and leave it when done
+    struct Request {
+        long long ticket = 0;
+        const double* b = nullptr;
+        double* x = nullptr;
+        int on_device = 0;
+        lqcd_mode mode = LQCD_MODE_AUTO;
+    };
+    struct SlotJob {
+        bool busy = false;
+        Request req;
+        lqcd_mode md = LQCD_MODE_PLAIN;
+        bool windowed = false;
+        bool deftol_pending = false;   // first leg of the DefTol restart still running
+        int first_iters = 0, first_matvecs = 0, first_ru = 0, outer = 0;
+        std::chrono::steady_clock::time_point t0;
+    };
+    struct Finished {
+        lqcd_solve_info info;
+        lqcd_status status;
+    };
+    std::deque<Request> queue;
+    SlotJob jobs[MAX_SLOTS];
+    std::map<long long, Finished> finished;
+    long long next_ticket = 1;
+    int eig_inflight = 0;
+    bool chunk_inflight = false;
+    bool session_busy() const {
+        if (!queue.empty() || chunk_inflight) return true;
+        for (int s = 0; s < kmax; ++s)
+            if (jobs[s].busy) return true;
+        return false;
+    }
 
     // last eigBiCG window info (per slot): final Ritz values
     std::vector<std::vector<double2>> last_ritz;
@@ -460,25 +497,29 @@ extern "C" lqcd_status lqcd_apply(lqcd_ctx* c, int dagger, lqcd_precision prec, 
 // ============================================================ deflation
 namespace {
 
-// x_hi[j] += U_r H^{-1} U_l^H (b_j - A x_hi[j]) for the first k slots.
-lqcd_status deflate_slots(lqcd_ctx* c, int k) {
+// x_hi[j] += U_r H^{-1} U_l^H (b_j - A x_hi[j]) for slots s0 .. s0+k-1.
+lqcd_status deflate_range(lqcd_ctx* c, int s0, int k) {
     const int n = c->n_def;
     if (n == 0 || k == 0) return LQCD_OK;
-    lqcd_status s = apply_fields(c, 0, 0, k, c->x_hi_all, c->dbytes, c->rt_all, c->dbytes, c->b_all);
+    double2* xh = c->x_hi_all + (size_t)s0 * c->N;
+    double2* rt = c->rt_all + (size_t)s0 * c->N;
+    lqcd_status s = apply_fields(c, 0, 0, k, xh, c->dbytes, rt, c->dbytes, c->b_all + (size_t)s0 * c->N);
     if (s != LQCD_OK) return s;
     double2* C = c->dsmall;   // n x k, ld k
-    const void* R = c->rt_all;
+    const void* R = rt;
     int rp = 0;
-    if (c->kprec) {   // FP32 projections: convert the residuals first
-        CK(launch_convert(c->rt_all, 0, c->x_lo_all, 1, (size_t)k * c->N, c->stream));
-        R = c->x_lo_all;
+    if (c->kprec) {   // FP32 projections: convert the residuals first (into these slots' x_lo)
+        void* xl = c->krylov(c->x_lo_all, s0);
+        CK(launch_convert(rt, 0, xl, 1, (size_t)k * c->N, c->stream));
+        R = xl;
         rp = 1;
     }
     CK(launch_multidot(n, c->Ul, c->kprec, k, R, rp, c->N, C, k, 0, c->mdscratch, c->mdscratch_elems, c->stream));
     CK(launch_lu_solve(n, c->Hlu, c->n_def_max, c->Hpiv, 0, k, C, k, c->stream));
-    CK(launch_vupdate(n, c->Ur, c->kprec, C, k, k, c->x_hi_all, 0, 0, c->N, c->stream));
+    CK(launch_vupdate(n, c->Ur, c->kprec, C, k, k, xh, 0, 0, c->N, c->stream));
     return LQCD_OK;
 }
+lqcd_status deflate_slots(lqcd_ctx* c, int k) { return deflate_range(c, 0, k); }
 
 lqcd_status refactor(lqcd_ctx* c) {
     const int n = c->n_def, ld = c->n_def_max;
@@ -698,42 +739,46 @@ lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol) {
     return LQCD_OK;
 }
 
+// Final Ritz vectors of one finished eigBiCG slot, appended to the eigenspace.
+lqcd_status grow_slot(lqcd_ctx* c, int s) {
+    const SlotState& st = c->h_state[s];
+    c->last_vs[s] = st.vs;
+    c->last_restarts[s] = st.restarts;
+    c->last_ritz[s].clear();
+    if (st.status != ST_CONVERGED) return LQCD_OK;
+    const int vs = st.vs;
+    const int nsel = std::min(c->nev, vs);
+    if (nsel == 0) return LQCD_OK;
+    const int room = c->n_def_max - c->n_def;
+    if (room <= 0) return LQCD_OK;
+    const int take = std::min(nsel, room);
+    double2* Yc = c->dsmall + (size_t)MAX_SMALL * MAX_SMALL * 2;
+    double2* Zc = Yc + (size_t)MAX_M * MAX_M;
+    double2* lam = Zc + (size_t)MAX_M * MAX_M;
+    int* nout = c->dinfo + 8;
+    CK(launch_final_ritz(c->d_state, c->d_ptrs, s, Yc, Zc, lam, nout, c->eigwork, c->stream));
+    std::vector<double2> hl(nsel);
+    CK(cudaMemcpyAsync(hl.data(), lam, sizeof(double2) * nsel, cudaMemcpyDeviceToHost, c->stream));
+    const SlotPtrs& P = c->h_ptrs[s];
+    // U = V Yc, Q = W Zc  into the next eigenspace columns (first 'take' of nsel)
+    CK(launch_vupdate(vs, P.V, c->kprec, Yc, nsel, take, c->krylov(c->Ur, c->n_def), c->kprec, 1, c->N, c->stream));
+    CK(launch_vupdate(vs, P.W, c->kprec, Zc, nsel, take, c->krylov(c->Ul, c->n_def), c->kprec, 1, c->N, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->last_ritz[s] = hl;
+    // work fields for [A V' | V'], [A^H W' | W']: this slot's window, which
+    // holds 2(m+1) > 4 nev Krylov fields
+    lqcd_status r = grow_space(c, take, P.V);
+    if (r != LQCD_OK) return r;
+    c->eig_rhs_done += 1;
+    return LQCD_OK;
+}
+
 // After an eigBiCG batch: final Ritz vectors of every slot, appended in slot order.
 lqcd_status grow_from_windows(lqcd_ctx* c, int k) {
-    for (int s = 0; s < k; ++s) {
-        c->last_vs[s] = c->h_state[s].vs;
-        c->last_restarts[s] = c->h_state[s].restarts;
-        c->last_ritz[s].clear();
-    }
     c->last_window_valid = 1;
     for (int s = 0; s < k; ++s) {
-        const SlotState& st = c->h_state[s];
-        if (st.status != ST_CONVERGED) continue;
-        const int vs = st.vs;
-        const int nsel = std::min(c->nev, vs);
-        if (nsel == 0) continue;
-        const int room = c->n_def_max - c->n_def;
-        if (room <= 0) break;
-        const int take = std::min(nsel, room);
-        double2* Yc = c->dsmall + (size_t)MAX_SMALL * MAX_SMALL * 2;
-        double2* Zc = Yc + (size_t)MAX_M * MAX_M;
-        double2* lam = Zc + (size_t)MAX_M * MAX_M;
-        int* nout = c->dinfo + 8;
-        CK(launch_final_ritz(c->d_state, c->d_ptrs, s, Yc, Zc, lam, nout, c->eigwork, c->stream));
-        std::vector<double2> hl(nsel);
-        CK(cudaMemcpyAsync(hl.data(), lam, sizeof(double2) * nsel, cudaMemcpyDeviceToHost, c->stream));
-        const SlotPtrs& P = c->h_ptrs[s];
-        // U = V Yc, Q = W Zc  into the next eigenspace columns (first 'take' of nsel)
-        CK(launch_vupdate(vs, P.V, c->kprec, Yc, nsel, take, c->krylov(c->Ur, c->n_def), c->kprec, 1, c->N, c->stream));
-        CK(launch_vupdate(vs, P.W, c->kprec, Zc, nsel, take, c->krylov(c->Ul, c->n_def), c->kprec, 1, c->N, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        c->last_ritz[s] = hl;
-        // work fields for [A V' | V'], [A^H W' | W']: this slot's window, which
-        // holds 2(m+1) > 4 nev Krylov fields
-        void* work = P.V;
-        lqcd_status r = grow_space(c, take, work);
+        lqcd_status r = grow_slot(c, s);
         if (r != LQCD_OK) return r;
-        c->eig_rhs_done += 1;
     }
     return LQCD_OK;
 }
@@ -753,6 +798,10 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx* c, int k, const double* b, double* x
                                   lqcd_solve_info* info) {
     if (!c || k < 0 || (k > 0 && (!b || !x))) return LQCD_ERR_ARG;
     if (mode < LQCD_MODE_AUTO || mode > LQCD_MODE_PLAIN) return LQCD_ERR_ARG;
+    if (c->session_busy()) {
+        g_last_error = "lqcd_solve: requests submitted with lqcd_submit are still in flight";
+        return LQCD_ERR_STATE;
+    }
     lqcd_status worst = LQCD_OK;
     for (int j0 = 0; j0 < k; j0 += c->kmax) {
         auto t0 = std::chrono::steady_clock::now();
@@ -1178,5 +1227,180 @@ extern "C" lqcd_status lqcd_apply_pair(lqcd_ctx* c, int variant, int k, const do
     }
     if (sigma)
         for (int s = 0; s < k; ++s) { sigma[2 * s] = out[s].sigma.x; sigma[2 * s + 1] = out[s].sigma.y; }
+    return LQCD_OK;
+}
+
+// ============================================================ serving session
+namespace {
+
+// One BiCG run in slot s from the x_hi and b already there: deflation of the
+// initial guess (phases 1 and 2 of Alg. Incremental eigBiCG), initial residual
+// and start vectors, with tolerance tol.
+lqcd_status begin_slot(lqcd_ctx* c, int s, lqcd_mode md, double tol) {
+    if (md != LQCD_MODE_PLAIN && c->n_def > 0) {
+        lqcd_status r = deflate_range(c, s, 1);
+        if (r != LQCD_OK) return r;
+    }
+    SlotState& st = c->h_state[s];
+    memset(&st, 0, sizeof(SlotState));
+    st.status = ST_RUNNING;
+    st.tol = tol;
+    st.maxiter = c->p.maxiter;
+    st.delta = c->kprec ? c->p.delta : 0.0;
+    st.m = md == LQCD_MODE_EIGBICG ? c->m : 0;
+    st.nev = c->nev;
+    CK(cudaMemcpyAsync(c->d_state + s, &st, sizeof(SlotState), cudaMemcpyHostToDevice, c->stream));
+    lqcd_status r = apply_fields(c, 0, 0, 1, c->x_hi_all + (size_t)s * c->N, c->dbytes,
+                                 c->rt_all + (size_t)s * c->N, c->dbytes, c->b_all + (size_t)s * c->N);
+    if (r != LQCD_OK) return r;
+    CK(launch_bicg_start(c->g, c->links64, c->p.kappa, c->kprec, c->d_state + s, c->d_ptrs + s, 1, c->N, c->stream));
+    return LQCD_OK;
+}
+
+// Start request req in free slot s. A deflated request with deftol > tol first
+// runs to deftol, is deflated again and then runs to tol (the DefTol restart),
+// exactly as lqcd_solve does.
+lqcd_status admit(lqcd_ctx* c, int s, const lqcd_ctx::Request& req) {
+    lqcd_ctx::SlotJob& job = c->jobs[s];
+    lqcd_mode md = req.mode;
+    if (md == LQCD_MODE_AUTO) md = c->eig_rhs_done + c->eig_inflight < c->p.n1 ? LQCD_MODE_EIGBICG : LQCD_MODE_DEFLATED;
+    lqcd_status r = upload(c, req.b, 1, c->b_all + (size_t)s * c->N, 0, req.on_device);
+    if (r != LQCD_OK) return r;
+    r = upload(c, req.x, 1, c->x_hi_all + (size_t)s * c->N, 0, req.on_device);
+    if (r != LQCD_OK) return r;
+    const bool two_legs = md == LQCD_MODE_DEFLATED && c->p.deftol > c->p.tol && c->n_def > 0;
+    r = begin_slot(c, s, md, two_legs ? c->p.deftol : c->p.tol);
+    if (r != LQCD_OK) return r;
+    job.busy = true;
+    job.req = req;
+    job.md = md;
+    job.windowed = md == LQCD_MODE_EIGBICG;
+    job.deftol_pending = two_legs;
+    job.first_iters = job.first_matvecs = job.first_ru = job.outer = 0;
+    job.t0 = std::chrono::steady_clock::now();
+    if (job.windowed) c->eig_inflight += 1;
+    return LQCD_OK;
+}
+
+// Slot s has stopped iterating: final FP64 residual; then either the second
+// leg of the DefTol restart, or eigenspace growth for an eigBiCG request and
+// the solution back to the caller's buffer.
+lqcd_status retire(lqcd_ctx* c, int s) {
+    lqcd_ctx::SlotJob& job = c->jobs[s];
+    CK(launch_bicg_finish(c->g, c->links64, c->p.kappa, c->kprec, c->d_state + s, c->d_ptrs + s, 1, c->N, c->stream));
+    CK(cudaMemcpyAsync(c->h_state + s, c->d_state + s, sizeof(SlotState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (job.deftol_pending) {
+        const SlotState& f = c->h_state[s];
+        job.first_iters = f.iter;
+        job.first_matvecs = f.matvecs;
+        job.first_ru = f.ru_count;
+        job.outer = 1;
+        job.deftol_pending = false;
+        return begin_slot(c, s, job.md, c->p.tol);
+    }
+    if (job.windowed) {
+        lqcd_status r = grow_slot(c, s);
+        if (r != LQCD_OK) return r;
+        c->last_window_valid = 1;
+        c->eig_inflight -= 1;
+    }
+    lqcd_status r = download(c, c->x_hi_all + (size_t)s * c->N, 0, 1, job.req.x, job.req.on_device);
+    if (r != LQCD_OK) return r;
+    CK(cudaStreamSynchronize(c->stream));
+    const SlotState& st = c->h_state[s];
+    lqcd_ctx::Finished f;
+    memset(&f.info, 0, sizeof(f.info));
+    f.info.iters = st.iter + job.first_iters;
+    f.info.matvecs = st.matvecs + job.first_matvecs;
+    f.info.restarts = st.restarts;
+    f.info.reliable_updates = st.ru_count + job.first_ru;
+    f.info.outer_steps = job.outer;
+    f.info.true_resid = st.bnorm > 0 ? st.true_rnorm / st.bnorm : 0.0;
+    f.info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - job.t0).count();
+    f.info.mode_used = job.md;
+    f.status = status_of(st);
+    if (f.status == LQCD_OK && st.bnorm > 0 && st.true_rnorm > c->p.tol * st.bnorm) f.status = LQCD_ERR_NOCONV;
+    c->finished[job.req.ticket] = f;
+    job.busy = false;
+    c->h_state[s].status = ST_IDLE;
+    return LQCD_OK;
+}
+
+}  // namespace
+
+extern "C" lqcd_status lqcd_submit(lqcd_ctx* c, const double* b, double* x, int on_device, lqcd_mode mode,
+                                   long long* ticket) {
+    if (!c || !b || !x || !ticket) return LQCD_ERR_ARG;
+    if (mode < LQCD_MODE_AUTO || mode > LQCD_MODE_PLAIN) return LQCD_ERR_ARG;
+    lqcd_ctx::Request r;
+    r.ticket = c->next_ticket++;
+    r.b = b;
+    r.x = x;
+    r.on_device = on_device ? 1 : 0;
+    r.mode = mode;
+    c->queue.push_back(r);
+    *ticket = r.ticket;
+    return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_progress(lqcd_ctx* c, int* pending) {
+    if (!c) return LQCD_ERR_ARG;
+    // 1. wait for the chunk in flight and read every slot's status
+    int herr = 0;
+    CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SlotState) * c->kmax, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->chunk_inflight = false;
+    if (herr) {
+        CK(cudaMemsetAsync(c->counters, 0, (size_t)c->kmax * CNT_COUNT * sizeof(unsigned), c->stream));
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        g_last_error = "operator kernel: bounded wait on a TMA copy timed out";
+        return LQCD_ERR_TIMEOUT;
+    }
+    // 2. retire slots that stopped iterating
+    for (int s = 0; s < c->kmax; ++s)
+        if (c->jobs[s].busy && c->h_state[s].status != ST_RUNNING) {
+            lqcd_status r = retire(c, s);
+            if (r != LQCD_OK) return r;
+        }
+    // 3. admit queued requests into free slots
+    for (int s = 0; s < c->kmax && !c->queue.empty(); ++s)
+        if (!c->jobs[s].busy) {
+            lqcd_ctx::Request req = c->queue.front();
+            c->queue.pop_front();
+            lqcd_status r = admit(c, s, req);
+            if (r != LQCD_OK) return r;
+        }
+    // 4. next chunk of iterations for every busy slot (asynchronous)
+    int busy = 0;
+    bool win = false;
+    for (int s = 0; s < c->kmax; ++s)
+        if (c->jobs[s].busy) {
+            ++busy;
+            win = win || c->jobs[s].windowed;
+        }
+    if (busy) {
+        lqcd_status r = run_chunk(c, c->kmax, win ? 1 : 0);
+        if (r != LQCD_OK) return r;
+        c->chunk_inflight = true;
+    }
+    if (pending) *pending = busy + (int)c->queue.size();
+    return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_poll(lqcd_ctx* c, long long ticket, int* done, lqcd_solve_info* info,
+                                 lqcd_status* result) {
+    if (!c || !done) return LQCD_ERR_ARG;
+    auto it = c->finished.find(ticket);
+    if (it == c->finished.end()) {
+        *done = 0;
+        return ticket > 0 && ticket < c->next_ticket ? LQCD_OK : LQCD_ERR_ARG;
+    }
+    *done = 1;
+    if (info) *info = it->second.info;
+    if (result) *result = it->second.status;
+    c->finished.erase(it);
     return LQCD_OK;
 }

@@ -98,6 +98,11 @@ def lib():
         L.lqcd_kernel_launches.restype = C.c_longlong
         L.lqcd_time_kernel.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
         L.lqcd_time_kernel.restype = C.c_int
+        L.lqcd_submit.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
+        L.lqcd_progress.argtypes = [vp, C.POINTER(C.c_int)]
+        L.lqcd_poll.argtypes = [vp, C.c_longlong, C.POINTER(C.c_int), C.POINTER(SolveInfo), C.POINTER(C.c_int)]
+        for name in ("lqcd_submit", "lqcd_progress", "lqcd_poll"):
+            getattr(L, name).restype = C.c_int
         L.lqcd_small_eig_noalloc.argtypes = [C.c_int, vp, vp, vp, vp, vp]
         L.lqcd_small_eig_noalloc.restype = C.c_int
         L.lqcd_apply_pair.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
@@ -219,6 +224,34 @@ class Solver:
         if raise_on_fail:
             _check(st, "lqcd_solve")
         return x, [infos[i].as_dict() for i in range(k)], st
+
+    # ------------------------------------------------------ serving session
+    def submit(self, b, x, mode="auto"):
+        """Queue one source; ``x`` holds the initial guess and receives the solution.
+        Both arrays must stay alive until :meth:`poll` reports the ticket done."""
+        pb, db = _ptr(b, self.n)
+        px, dx = _ptr(x, self.n)
+        if db != dx:
+            raise ValueError("b and x must both be host or both be device arrays")
+        t = C.c_longlong()
+        _check(lib().lqcd_submit(self._h, pb, px, db, _MODES[mode] if isinstance(mode, str) else int(mode),
+                                 C.byref(t)), "lqcd_submit")
+        return t.value
+
+    def progress(self):
+        """Retire finished requests, admit queued ones, launch the next iterations;
+        returns the number of requests still queued or running."""
+        n = C.c_int()
+        _check(lib().lqcd_progress(self._h, C.byref(n)), "lqcd_progress")
+        return n.value
+
+    def poll(self, ticket):
+        """``(done, info, status)`` of a submitted request (reported once)."""
+        done = C.c_int()
+        info = SolveInfo()
+        res = C.c_int()
+        _check(lib().lqcd_poll(self._h, int(ticket), C.byref(done), C.byref(info), C.byref(res)), "lqcd_poll")
+        return bool(done.value), (info.as_dict() if done.value else None), res.value
 
     def deflate(self, b, x0):
         b = _as_batch(b, self.n)
