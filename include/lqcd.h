@@ -148,8 +148,11 @@ lqcd_status lqcd_submit(lqcd_ctx *ctx, const double *b, double *x, int on_device
  * requests (final FP64 residual, eigenspace growth, solution written), admit
  * queued requests into free slots (deflation, start vectors) and launch the
  * next chunk of 8 BiCG iterations for every busy slot without waiting for it.
+ * wait = 0: if the chunk in flight has not finished yet, return at once and
+ * change nothing (lets one host thread drive several contexts, each on its
+ * own stream); wait != 0: block until it has.
  * *pending = requests queued or in slots (may be NULL). */
-lqcd_status lqcd_progress(lqcd_ctx *ctx, int *pending);
+lqcd_status lqcd_progress(lqcd_ctx *ctx, int wait, int *pending);
 
 /* Completion of a submitted request: *done = 1 and *info / *result (the solve's
  * own status, e.g. LQCD_ERR_NOCONV) once it finished (each reported once);
@@ -235,6 +238,19 @@ int lqcd_dslash_variant(const lqcd_ctx *ctx);
  * use; LQCD_ERR_TIMEOUT if a bounded wait in the kernel gave up. */
 lqcd_status lqcd_apply_pair(lqcd_ctx *ctx, int variant, int k, const double *p, const double *phat,
                             double *Ap, double *Ahp, double *sigma);
+
+/* Inner-product matrix of FP32 fields, the Galerkin projections of the
+ * deflation and the eigenspace growth (Sec. 2, Alg. Incremental eigBiCG:
+ * U_l^H r and U_l^H A U_r): C[i*b + j] = sum_e conj(X_i(e)) Y_j(e) for i < a,
+ * j < b.  X, Y: DEVICE pointers to a (resp. b) consecutive fields of n complex
+ * FP32 numbers (re, im interleaved, 16-byte aligned).  C: HOST, a*b complex
+ * (2ab doubles).  path 0 = CUDA cores (FP32 products, FP64 block sums),
+ * path 1 = tensor cores (3xTF32 tcgen05 MMAs, FP32 runs summed in FP64;
+ * needs 2n divisible by 32 and a <= 512, else LQCD_ERR_ARG).  With reps > 0
+ * the call is repeated reps more times and *avg_ms receives the mean device
+ * time of one call.  Allocates its scratch; synchronises the device. */
+lqcd_status lqcd_field_dots(int a, const float *X, int b, const float *Y, long long n, int path, int reps,
+                            double *C, double *avg_ms);
 
 /* Allocation-free eigen-solver (no counterpart in the paper; a service for
  * callers that cannot allocate device memory when they need a small

@@ -191,9 +191,10 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Block-wide sum of nvals complex doubles per thread; result valid in thread 0.
-// blockDim.x must be a multiple of 32 and <= 1024. smem: 32*nvals double2.
-template <int NV> __device__ __forceinline__ void block_sum(double2 (&v)[NV], double2* smem) {
+// Block-wide sum of NV complex values per thread (float2 or double2, summed in
+// that precision); result valid in thread 0.
+// blockDim.x must be a multiple of 32 and <= 1024. smem: 32*NV values of type C.
+template <int NV, typename C> __device__ __forceinline__ void block_sum(C (&v)[NV], C* smem) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
@@ -206,7 +207,9 @@ template <int NV> __device__ __forceinline__ void block_sum(double2 (&v)[NV], do
     if (w == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            double2 t = lane < nw ? smem[lane * NV + i] : make_double2(0.0, 0.0);
+            C t;
+            t.x = 0; t.y = 0;
+            if (lane < nw) t = smem[lane * NV + i];
             v[i] = warp_sum(t);
         }
     }

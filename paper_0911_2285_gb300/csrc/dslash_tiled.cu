@@ -13,6 +13,7 @@
 // timeout sets an error word for the host and the CTA stops issuing work.
 #include <stdint.h>
 
+#include "async.cuh"
 #include "dslash.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
@@ -21,40 +22,6 @@ namespace lqcd {
 namespace {
 
 constexpr int TILE_MAX_THREADS = 256;
-constexpr long long WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Wait for the phase of the given parity to complete, at most WAIT_CYCLES.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    const long long t0 = clock64();
-    while (!mbar_test(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
-    return true;
-}
-
 struct SmemTile {
     const float4* s;   // base of one plane-row block: [6 chunks][ld sites]
     int ld;
@@ -123,7 +90,7 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, 1)
     __shared__ int issued[5];   // phases started on each barrier (copies possibly in flight)
     if (threadIdx.x == 0) {
         for (int i = 0; i < 5; ++i) { mbar_init(&bars[i], 1); issued[i] = 0; }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init_fence();
     }
     __syncthreads();
 
@@ -251,7 +218,7 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, 1)
         __syncthreads();
         return;
     }
-    double2 v[2];
+    float2 v[2];
     sacc.to(v);
     double2 tot[2];
     const unsigned nblk = (unsigned)(tg.nyb * Lz * tg.nseg);

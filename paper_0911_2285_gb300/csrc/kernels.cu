@@ -122,17 +122,17 @@ __global__ void __launch_bounds__(BL_THREADS) multidot_kernel(int a, const void*
                     if (j < b) acc[i][j] = acc[i][j] + cdot(x, y[j]);
             }
     }
-    double2 v[MD_TI * MD_BMAX];
+    C v[MD_TI * MD_BMAX];
 #pragma unroll
     for (int i = 0; i < MD_TI; ++i)
 #pragma unroll
-        for (int j = 0; j < MD_BMAX; ++j) v[i * MD_BMAX + j] = to_d(acc[i][j]);
-    __shared__ double2 sm[(BL_THREADS / 32) * MD_TI * MD_BMAX];
-    block_sum<MD_TI * MD_BMAX>(v, sm);
+        for (int j = 0; j < MD_BMAX; ++j) v[i * MD_BMAX + j] = acc[i][j];
+    __shared__ C sm[(BL_THREADS / 32) * MD_TI * MD_BMAX];
+    block_sum<MD_TI * MD_BMAX>(v, sm);   // in the accumulation precision T
     if (threadIdx.x == 0) {
         double2* out = scratch + ((size_t)by * nbx + bx) * (MD_TI * MD_BMAX);
 #pragma unroll
-        for (int q = 0; q < MD_TI * MD_BMAX; ++q) out[q] = v[q];
+        for (int q = 0; q < MD_TI * MD_BMAX; ++q) out[q] = to_d(v[q]);
     }
 }
 __global__ void multidot_reduce_kernel(int a, int b, int nbx, const double2* scratch, double2* Cm, int ldc,
@@ -190,10 +190,10 @@ __global__ void __launch_bounds__(BL_THREADS) norms_kernel(const void* Y, size_t
     S acc = S(0);
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x)
         acc += abs2(y[e]);
-    double2 v[1] = {make_double2((double)acc, 0.0)};
-    __shared__ double2 sm[BL_THREADS / 32];
+    cplx<S> v[1] = {mk<S>(acc, S(0))};
+    __shared__ cplx<S> sm[BL_THREADS / 32];
     block_sum<1>(v, sm);
-    if (threadIdx.x == 0) scratch[(size_t)j * gridDim.x + blockIdx.x] = v[0];
+    if (threadIdx.x == 0) scratch[(size_t)j * gridDim.x + blockIdx.x] = to_d(v[0]);
 }
 __global__ void norms_reduce_kernel(int b, int nb, const double2* scratch, double* out) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
         acc.a += abs2(r.a) + abs2(r.b);
         acc.b += (S)(cabs2(bb.a) + cabs2(bb.b));
     }
-    double2 v[2];
+    cplx<S> v[2];
     acc.to(v);
     double2 tot[2];
     if (reduce_slot<2>(P, CNT_START, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
         }
         if (which) return;
     }
-    double2 v[2];
+    cplx<S> v[2];
     sacc.to(v);
     double2 tot[2];
     if (reduce_slot<2>(P, CNT_MATVEC, v, tot, nsb, sblock) && threadIdx.x == 0) {
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, c
         acc.a += abs2(r.a) + abs2(r.b);
         acc.b += abs2(h.a) + abs2(h.b);
     }
-    double2 v[2];
+    cplx<S> v[2];
     acc.to(v);
     double2 tot[2];
     if (reduce_slot<2>(P, CNT_UPDATE, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(BL_THREADS) replace_kernel(SlotState* states, 
             rho = rho + cdot(h.a, r.a) + cdot(h.b, r.b);
         }
     }
-    double2 v[1] = {to_d(rho)};
+    cplx<S> v[1] = {rho};
     double2 tot[1];
     if (reduce_slot<1>(P, CNT_REPLACE, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
         if (run) {
@@ -783,9 +783,17 @@ cudaError_t launch_convert(const void* src, int sp, void* dst, int dp, size_t n,
     return cudaGetLastError();
 }
 
+static int g_dots_path = 1;   // 1: tensor cores for FP32 x FP32 when the shape allows
+void set_dots_path(int path) { g_dots_path = path; }
+
 cudaError_t launch_multidot(int a, const void* X, int xp, int b, const void* Y, int yp, size_t N, double2* Cm,
-                            int ldc, int conj_store, double2* scratch, size_t scratch_elems, cudaStream_t st) {
+                            int ldc, int conj_store, double2* scratch, size_t scratch_elems, cudaStream_t st,
+                            int* err) {
     if (a <= 0 || b <= 0) return cudaSuccess;
+    if (g_dots_path == 1 && xp == 1 && yp == 1 && dots_tc_supported(a, X, Y, N) &&
+        dots_tc_scratch_doubles(a) <= 2 * scratch_elems)
+        return launch_dots_tc(a, X, N * 8, b, Y, N * 8, N, Cm, ldc, conj_store, reinterpret_cast<double*>(scratch),
+                              2 * scratch_elems, err, st);
     for (int j0 = 0; j0 < b; j0 += MD_BMAX) {
         const int bb = b - j0 < MD_BMAX ? b - j0 : MD_BMAX;
         const int nby = div_up(a, MD_TI);

@@ -39,7 +39,19 @@ cudaError_t launch_convert(const void* src, int src_prec, void* dst, int dst_pre
 // conj_store: store conj(C) transposed, C[j*ldc + i] instead.
 cudaError_t launch_multidot(int a, const void* X, int xprec, int b, const void* Y, int yprec,
                             size_t N, double2* C, int ldc, int conj_store, double2* scratch,
-                            size_t scratch_elems, cudaStream_t st);
+                            size_t scratch_elems, cudaStream_t st, int* err = nullptr);
+// 1 (default): FP32 x FP32 products go to the tensor-core path where it applies; 0: CUDA cores.
+void set_dots_path(int path);
+// Tensor-core form of launch_multidot for FP32 X and Y (gemm_tc.cu): 3xTF32
+// tcgen05 MMAs, split-K over the SMs, partials summed in FP64. Fields of X
+// (resp. Y) are x_stride (y_stride) bytes apart. scratch: dots_tc_scratch_doubles(a)
+// doubles. err: device word set to 1 if a bounded wait gave up.
+bool dots_tc_supported(int a, const void* X, const void* Y, size_t N);
+size_t dots_tc_scratch_doubles(int a);
+cudaError_t prepare_dots_tc();
+cudaError_t launch_dots_tc(int a, const void* X, size_t x_stride, int b, const void* Y, size_t y_stride, size_t N,
+                           double2* C, int ldc, int conj_store, double* scratch, size_t scratch_doubles, int* err,
+                           cudaStream_t st);
 // overwrite = 0: Y_j += sum_i X_i D[i*ldd + j];  overwrite = 1: Y_j = sum_i X_i D[i*ldd + j].
 // The arithmetic is FP32 when X is FP32 (the sum is added to an FP64 Y in FP64).
 cudaError_t launch_vupdate(int a, const void* X, int xprec, const double2* D, int ldd, int b,

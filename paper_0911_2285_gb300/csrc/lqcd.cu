@@ -138,6 +138,7 @@ struct lqcd_ctx {
     long long next_ticket = 1;
     int eig_inflight = 0;
     bool chunk_inflight = false;
+    cudaEvent_t chunk_ev = nullptr;    // recorded after each session chunk
     bool session_busy() const {
         if (!queue.empty() || chunk_inflight) return true;
         for (int s = 0; s < kmax; ++s)
@@ -391,6 +392,7 @@ extern "C" void lqcd_destroy(lqcd_ctx* c) {
             if (c->graphs[i][j]) cudaGraphExecDestroy(c->graphs[i][j]);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->chunk_ev) cudaEventDestroy(c->chunk_ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -514,7 +516,7 @@ lqcd_status deflate_range(lqcd_ctx* c, int s0, int k) {
         R = xl;
         rp = 1;
     }
-    CK(launch_multidot(n, c->Ul, c->kprec, k, R, rp, c->N, C, k, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_multidot(n, c->Ul, c->kprec, k, R, rp, c->N, C, k, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
     CK(launch_lu_solve(n, c->Hlu, c->n_def_max, c->Hpiv, 0, k, C, k, c->stream));
     CK(launch_vupdate(n, c->Ur, c->kprec, C, k, k, xh, 0, 0, c->N, c->stream));
     return LQCD_OK;
@@ -555,8 +557,8 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, void* work) {
     CK(launch_norms(nn, Wn, kp, c->N, nrm + nn, c->mdscratch, c->mdscratch_elems, c->stream));
     if (n > 0) {
         // V' = V - U_r M^{-1} U_l^H V ;  W' = W - U_l M^{-H} U_r^H W
-        CK(launch_multidot(n, c->Ul, kp, nn, Vn, kp, c->N, G, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
-        CK(launch_multidot(n, c->Ur, kp, nn, Wn, kp, c->N, G2, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+        CK(launch_multidot(n, c->Ul, kp, nn, Vn, kp, c->N, G, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
+        CK(launch_multidot(n, c->Ur, kp, nn, Wn, kp, c->N, G2, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
         CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 0, nn, G, nn, c->stream));
         CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 1, nn, G2, nn, c->stream));
         negate_kernel<<<1, 256, 0, c->stream>>>(G, n * nn);
@@ -606,14 +608,14 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, void* work) {
     CK(cudaMemcpyAsync(AW + (size_t)kk * c->kbytes, Wn, (size_t)kk * c->kbytes, cudaMemcpyDeviceToDevice, c->stream));
     // [U_l W']^H [A V' | V'] -> H[:, n:n+kk] and M[:, n:n+kk]  (rows 0..n+kk)
     const int nt = n + kk;
-    CK(launch_multidot(nt, c->Ul, kp, 2 * kk, AV, kp, c->N, T1, 2 * kk, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_multidot(nt, c->Ul, kp, 2 * kk, AV, kp, c->N, T1, 2 * kk, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
     copy_block_kernel<<<16, 256, 0, c->stream>>>(T1, 2 * kk, c->Hdef + n, ld, nt, kk);
     copy_block_kernel<<<16, 256, 0, c->stream>>>(T1 + kk, 2 * kk, c->Mdef + n, ld, nt, kk);
     count_launches(2);
     CK(cudaGetLastError());
     if (n > 0) {
         // (A^H W')^H U_r -> H[n:n+kk, 0:n] ;  W'^H U_r -> M[n:n+kk, 0:n]
-        CK(launch_multidot(n, c->Ur, kp, 2 * kk, AW, kp, c->N, T2, n, 1, c->mdscratch, c->mdscratch_elems, c->stream));
+        CK(launch_multidot(n, c->Ur, kp, 2 * kk, AW, kp, c->N, T2, n, 1, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
         copy_block_kernel<<<16, 256, 0, c->stream>>>(T2, n, c->Hdef + (size_t)n * ld, ld, kk, n);
         copy_block_kernel<<<16, 256, 0, c->stream>>>(T2 + (size_t)kk * n, n, c->Mdef + (size_t)n * ld, ld, kk, n);
         count_launches(2);
@@ -891,9 +893,9 @@ lqcd_status project_fp64(lqcd_ctx* c, int n, double2* Hout, double2* Mout, int l
         lqcd_status s = apply_fields(c, 0, 0, kb, in, c->kprec ? c->dbytes : c->kbytes, c->rt_all, c->dbytes, nullptr);
         if (s != LQCD_OK) return s;
         CK(launch_multidot(n, c->Ul, c->kprec, kb, c->rt_all, 0, c->N, Hout + j0, ld, 0, c->mdscratch,
-                           c->mdscratch_elems, c->stream));
+                           c->mdscratch_elems, c->stream, c->d_err));
         CK(launch_multidot(n, c->Ul, c->kprec, kb, in, 0, c->N, Mout + j0, ld, 0, c->mdscratch,
-                           c->mdscratch_elems, c->stream));
+                           c->mdscratch_elems, c->stream, c->d_err));
     }
     return LQCD_OK;
 }
@@ -983,8 +985,8 @@ extern "C" lqcd_status lqcd_eigs(lqcd_ctx* c, int* n_inout, double* evals, doubl
             CK(launch_vupdate(kb, c->x_hi_all, 0, D, kb, kb, c->rt_all, 0, 0, c->N, c->stream));
             double2* gr = D + 256;
             double2* gu = gr + 256;
-            CK(launch_multidot(kb, c->rt_all, 0, kb, c->rt_all, 0, c->N, gr, kb, 0, c->mdscratch, c->mdscratch_elems, c->stream));
-            CK(launch_multidot(kb, c->x_hi_all, 0, kb, c->x_hi_all, 0, c->N, gu, kb, 0, c->mdscratch, c->mdscratch_elems, c->stream));
+            CK(launch_multidot(kb, c->rt_all, 0, kb, c->rt_all, 0, c->N, gr, kb, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
+            CK(launch_multidot(kb, c->x_hi_all, 0, kb, c->x_hi_all, 0, c->N, gu, kb, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
             std::vector<double2> hr((size_t)kb * kb), hu((size_t)kb * kb);
             CK(cudaMemcpyAsync(hr.data(), gr, sizeof(double2) * kb * kb, cudaMemcpyDeviceToHost, c->stream));
             CK(cudaMemcpyAsync(hu.data(), gu, sizeof(double2) * kb * kb, cudaMemcpyDeviceToHost, c->stream));
@@ -1050,6 +1052,56 @@ extern "C" lqcd_status lqcd_small_eig(int n, const double* C, double* evals, dou
         else if (info) { g_last_error = "QR iteration did not converge"; ret = LQCD_ERR_NOCONV; }
     }
     cudaFree(dA); cudaFree(dl); cudaFree(dY); cudaFree(dZ); cudaFree(dw); cudaFree(dinfo);
+    return ret;
+}
+
+extern "C" lqcd_status lqcd_field_dots(int a, const float* X, int b, const float* Y, long long n, int path, int reps,
+                                       double* C, double* avg_ms) {
+    if (a < 1 || b < 1 || n < 1 || !X || !Y || !C || (path != 0 && path != 1) || reps < 0 || (reps > 0 && !avg_ms))
+        return LQCD_ERR_ARG;
+    const size_t N = (size_t)n;
+    if (path == 1 && !dots_tc_supported(a, X, Y, N)) {
+        g_last_error = "tensor-core path needs 2n % 32 == 0, a <= 512 and 16-byte aligned fields";
+        return LQCD_ERR_ARG;
+    }
+    const size_t md_elems = std::max((size_t)((a + 3) / 4) * 1216 * 32, dots_tc_scratch_doubles(a) / 2 + 1);
+    double2 *scratch = nullptr, *dC = nullptr;
+    int* derr = nullptr;
+    lqcd_status ret = LQCD_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&scratch, md_elems * 16)) != cudaSuccess || (e = cudaMalloc(&dC, (size_t)a * b * 16)) != cudaSuccess ||
+        (e = cudaMalloc(&derr, 16)) != cudaSuccess) {
+        set_error("cudaMalloc", e);
+        ret = LQCD_ERR_OOM;
+    }
+    if (ret == LQCD_OK) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        e = cudaMemset(derr, 0, 16);
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        set_dots_path(path);
+        for (int r = 0; e == cudaSuccess && r <= reps; ++r) {
+            if (r == 1) e = cudaEventRecord(e0, 0);
+            if (e == cudaSuccess)
+                e = launch_multidot(a, X, 1, b, Y, 1, N, dC, b, 0, scratch, md_elems, 0, derr);
+        }
+        set_dots_path(1);
+        if (e == cudaSuccess && reps > 0) e = cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess && reps > 0) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, e0, e1);
+            *avg_ms = ms / reps;
+        }
+        int herr = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(C, dC, (size_t)a * b * 16, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { set_error("field dots", e); ret = LQCD_ERR_CUDA; }
+        else if (herr) { g_last_error = "tensor-core dots: a bounded wait timed out"; ret = LQCD_ERR_TIMEOUT; }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+    cudaFree(scratch); cudaFree(dC); cudaFree(derr);
     return ret;
 }
 
@@ -1344,8 +1396,20 @@ extern "C" lqcd_status lqcd_submit(lqcd_ctx* c, const double* b, double* x, int 
     return LQCD_OK;
 }
 
-extern "C" lqcd_status lqcd_progress(lqcd_ctx* c, int* pending) {
+extern "C" lqcd_status lqcd_progress(lqcd_ctx* c, int wait, int* pending) {
     if (!c) return LQCD_ERR_ARG;
+    if (!wait && c->chunk_inflight) {
+        cudaError_t q = cudaEventQuery(c->chunk_ev);
+        if (q == cudaErrorNotReady) {
+            if (pending) {
+                int busy = 0;
+                for (int s = 0; s < c->kmax; ++s) busy += c->jobs[s].busy ? 1 : 0;
+                *pending = busy + (int)c->queue.size();
+            }
+            return LQCD_OK;
+        }
+        if (q != cudaSuccess) { set_error("cudaEventQuery", q); return LQCD_ERR_CUDA; }
+    }
     // 1. wait for the chunk in flight and read every slot's status
     int herr = 0;
     CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SlotState) * c->kmax, cudaMemcpyDeviceToHost, c->stream));
@@ -1384,6 +1448,8 @@ extern "C" lqcd_status lqcd_progress(lqcd_ctx* c, int* pending) {
     if (busy) {
         lqcd_status r = run_chunk(c, c->kmax, win ? 1 : 0);
         if (r != LQCD_OK) return r;
+        if (!c->chunk_ev) CK(cudaEventCreateWithFlags(&c->chunk_ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(c->chunk_ev, c->stream));
         c->chunk_inflight = true;
     }
     if (pending) *pending = busy + (int)c->queue.size();

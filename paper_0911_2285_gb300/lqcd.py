@@ -99,10 +99,13 @@ def lib():
         L.lqcd_time_kernel.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
         L.lqcd_time_kernel.restype = C.c_int
         L.lqcd_submit.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
-        L.lqcd_progress.argtypes = [vp, C.POINTER(C.c_int)]
+        L.lqcd_progress.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.lqcd_poll.argtypes = [vp, C.c_longlong, C.POINTER(C.c_int), C.POINTER(SolveInfo), C.POINTER(C.c_int)]
         for name in ("lqcd_submit", "lqcd_progress", "lqcd_poll"):
             getattr(L, name).restype = C.c_int
+        L.lqcd_field_dots.argtypes = [C.c_int, vp, C.c_int, vp, C.c_longlong, C.c_int, C.c_int, vp,
+                                      C.POINTER(C.c_double)]
+        L.lqcd_field_dots.restype = C.c_int
         L.lqcd_small_eig_noalloc.argtypes = [C.c_int, vp, vp, vp, vp, vp]
         L.lqcd_small_eig_noalloc.restype = C.c_int
         L.lqcd_apply_pair.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
@@ -238,11 +241,12 @@ class Solver:
                                  C.byref(t)), "lqcd_submit")
         return t.value
 
-    def progress(self):
+    def progress(self, wait=True):
         """Retire finished requests, admit queued ones, launch the next iterations;
-        returns the number of requests still queued or running."""
+        returns the number of requests still queued or running. With ``wait=False``
+        it returns at once while the iterations in flight are still running."""
         n = C.c_int()
-        _check(lib().lqcd_progress(self._h, C.byref(n)), "lqcd_progress")
+        _check(lib().lqcd_progress(self._h, 1 if wait else 0, C.byref(n)), "lqcd_progress")
         return n.value
 
     def poll(self, ticket):
@@ -370,6 +374,27 @@ def _zeros_like(a):
 def kernel_launches():
     """Kernels launched by the library in this process so far."""
     return int(lib().lqcd_kernel_launches())
+
+
+def field_dots(X, Y, path=1, reps=0):
+    """``C = X^H Y`` (a x b, complex128) of FP32 fields: ``X`` (a, n) and ``Y`` (b, n)
+    contiguous complex64 CUDA tensors. ``path`` 0 = CUDA cores, 1 = tensor cores
+    (3xTF32). Returns ``(C, avg_ms)``; ``avg_ms`` is the mean time of ``reps`` more
+    calls (None when ``reps == 0``)."""
+    import torch
+    for t in (X, Y):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()
+                and t.dim() == 2):
+            raise TypeError("X and Y must be contiguous 2-D complex64 CUDA tensors")
+    if X.shape[1] != Y.shape[1]:
+        raise ValueError("X and Y fields must have the same length")
+    a, n = X.shape
+    b = Y.shape[0]
+    out = np.zeros((a, b), dtype=np.complex128)
+    ms = C.c_double()
+    _check(lib().lqcd_field_dots(a, C.c_void_p(X.data_ptr()), b, C.c_void_p(Y.data_ptr()), n, int(path), int(reps),
+                                 C.c_void_p(out.ctypes.data), C.byref(ms)), "lqcd_field_dots")
+    return out, (ms.value if reps > 0 else None)
 
 
 def small_eig(c):

@@ -103,24 +103,27 @@ class Server:
                 r.ticket = self.ops[r.op].submit(r.b, r.x, mode=mode)
                 pending[r.op][r.ticket] = r
                 i += 1
-            # advance every operator that has work (each on its own stream)
-            for name, solver in self.ops.items():
-                if pending[name] or active[name]:
-                    active[name] = solver.progress()
-                    for ticket in list(pending[name]):
-                        done, info, status = solver.poll(ticket)
-                        if done:
-                            r = pending[name].pop(ticket)
-                            r.t_done = time.perf_counter() - t0
-                            r.info, r.status = info, status
-                            rep.latencies.append(r.t_done - r.t_arrival)
-                            if status == 0:
-                                rep.completed += 1
-                            else:
-                                rep.failed += 1
+            # advance every operator that has work (each on its own stream); block on
+            # one only when nothing else can happen meanwhile
+            busy = [n for n in self.ops if pending[n] or active[n]]
+            wait = len(busy) == 1 and (not realtime or i == len(reqs))
+            for name in busy:
+                solver = self.ops[name]
+                active[name] = solver.progress(wait=wait)
+                for ticket in list(pending[name]):
+                    done, info, status = solver.poll(ticket)
+                    if done:
+                        r = pending[name].pop(ticket)
+                        r.t_done = time.perf_counter() - t0
+                        r.info, r.status = info, status
+                        rep.latencies.append(r.t_done - r.t_arrival)
+                        if status == 0:
+                            rep.completed += 1
+                        else:
+                            rep.failed += 1
             if realtime and i < len(reqs) and not any(active.values()) and not any(pending.values()):
-                wait = reqs[i].t_arrival - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(wait)
+                wait_s = reqs[i].t_arrival - (time.perf_counter() - t0)
+                if wait_s > 0:
+                    time.sleep(wait_s)
         rep.makespan = time.perf_counter() - t0
         return rep, reqs

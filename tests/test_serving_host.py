@@ -20,7 +20,7 @@ class FakeSolver:
         self.queue.append((t, b, x))
         return t
 
-    def progress(self):
+    def progress(self, wait=True):
         for t in list(self.slots):
             self.slots[t][0] -= 1
             if self.slots[t][0] == 0:
