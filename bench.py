@@ -112,8 +112,9 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- profiles
-def recorded_traffic(kernel_tag):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+def recorded_traffic(kernel_tag, variant):
+    """DRAM bytes per launch of operator-kernel shape ``variant`` from the committed ncu
+    summary, if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
     if not os.path.exists(path):
         return None
@@ -126,7 +127,7 @@ def recorded_traffic(kernel_tag):
     if vals.get("source_sha256") != src:
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[f"dram_bytes_per_launch_variant_{variant}"])
     except (KeyError, ValueError):
         return None
 
@@ -301,8 +302,8 @@ def main_ours(args):
     achieved = alg_bytes / (op_ms / 1e3) / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    traffic = recorded_traffic(f"dhop_pair_f32_k{k}_{args.workload.replace('^', '').replace('x', 'x')}")
     shape = s.dslash_variant()
+    traffic = recorded_traffic(f"dhop_pair_f32_k{k}_{'x'.join(str(d) for d in w['dims'])}", shape)
     upd_ms = s.time_kernel(1, k, reps)
     dir_ms = s.time_kernel(2, k, reps)
 

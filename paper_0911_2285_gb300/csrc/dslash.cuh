@@ -25,6 +25,19 @@ struct LinksD {   // FP64, all 18 reals
     }
 };
 
+// conj(a b - c d) as two fused chains.
+__device__ __forceinline__ float2 cross_conj(float2 a, float2 b, float2 c, float2 d) {
+    float re = a.x * b.x;
+    re = fmaf(-a.y, b.y, re);
+    re = fmaf(-c.x, d.x, re);
+    re = fmaf(c.y, d.y, re);
+    float im = c.x * d.y;
+    im = fmaf(c.y, d.x, im);
+    im = fmaf(-a.x, b.y, im);
+    im = fmaf(-a.y, b.x, im);
+    return make_float2(re, im);
+}
+
 struct LinksF {   // FP32 rows 0, 1; row 2 rebuilt as conj(row0 x row1)
     const float4* u;
     int V;
@@ -35,9 +48,9 @@ struct LinksF {   // FP32 rows 0, 1; row 2 rebuilt as conj(row0 x row1)
         m[0][0] = make_float2(a.x, a.y); m[0][1] = make_float2(a.z, a.w);
         m[0][2] = make_float2(b.x, b.y); m[1][0] = make_float2(b.z, b.w);
         m[1][1] = make_float2(c.x, c.y); m[1][2] = make_float2(c.z, c.w);
-        m[2][0] = conj_(m[0][1] * m[1][2] - m[0][2] * m[1][1]);
-        m[2][1] = conj_(m[0][2] * m[1][0] - m[0][0] * m[1][2]);
-        m[2][2] = conj_(m[0][0] * m[1][1] - m[0][1] * m[1][0]);
+        m[2][0] = cross_conj(m[0][1], m[1][2], m[0][2], m[1][1]);
+        m[2][1] = cross_conj(m[0][2], m[1][0], m[0][0], m[1][2]);
+        m[2][2] = cross_conj(m[0][0], m[1][1], m[0][1], m[1][0]);
     }
 };
 
@@ -79,19 +92,52 @@ __device__ __forceinline__ void reconstruct(const C (&uh)[2][3], C (&acc)[12]) {
     }
 }
 
+// Fused multiply-add chains (one rounding per term, no separate product and
+// sum instructions): o = u h and o = u^+ h for the two spin rows of h.
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+
 template <typename C>
 __device__ __forceinline__ void su3_mul(const C (&u)[3][3], const C (&h)[2][3], C (&o)[2][3]) {
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int r = 0; r < 3; ++r) o[a][r] = u[r][0] * h[a][0] + u[r][1] * h[a][1] + u[r][2] * h[a][2];
+        for (int r = 0; r < 3; ++r) {
+            auto re = u[r][0].x * h[a][0].x;
+            auto im = u[r][0].x * h[a][0].y;
+            re = fma_(-u[r][0].y, h[a][0].y, re);
+            im = fma_(u[r][0].y, h[a][0].x, im);
+#pragma unroll
+            for (int c = 1; c < 3; ++c) {
+                re = fma_(u[r][c].x, h[a][c].x, re);
+                im = fma_(u[r][c].x, h[a][c].y, im);
+                re = fma_(-u[r][c].y, h[a][c].y, re);
+                im = fma_(u[r][c].y, h[a][c].x, im);
+            }
+            o[a][r].x = re;
+            o[a][r].y = im;
+        }
 }
 template <typename C>
 __device__ __forceinline__ void su3_dag_mul(const C (&u)[3][3], const C (&h)[2][3], C (&o)[2][3]) {
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int r = 0; r < 3; ++r) o[a][r] = cdot(u[0][r], h[a][0]) + cdot(u[1][r], h[a][1]) + cdot(u[2][r], h[a][2]);
+        for (int r = 0; r < 3; ++r) {
+            auto re = u[0][r].x * h[a][0].x;
+            auto im = u[0][r].x * h[a][0].y;
+            re = fma_(u[0][r].y, h[a][0].y, re);
+            im = fma_(-u[0][r].y, h[a][0].x, im);
+#pragma unroll
+            for (int c = 1; c < 3; ++c) {
+                re = fma_(u[c][r].x, h[a][c].x, re);
+                im = fma_(u[c][r].x, h[a][c].y, im);
+                re = fma_(u[c][r].y, h[a][c].y, re);
+                im = fma_(-u[c][r].y, h[a][c].x, im);
+            }
+            o[a][r].x = re;
+            o[a][r].y = im;
+        }
 }
 
 // Input accessors: in.load(site, psi) fills 12 complex values.

@@ -1,0 +1,63 @@
+"""Time single kernels of the library on a synthetic lattice (also the workload of
+the committed ncu captures).
+
+    python -m paper_0911_2285_gb300.kernelbench dhop --workload 16^3x32 --variants 2 4
+    python -m paper_0911_2285_gb300.kernelbench dots --a 80 --b 8 --n 1572864
+
+``dhop``: the operator-pair kernel shapes (A p, A^+ phat for k slots) through
+``Solver.time_kernel``; after the timed runs each listed shape is launched once
+more (the launches an ncu capture skips to). ``dots``: the inner-product matrix
+X^H Y of FP32 fields on the tensor cores and on the CUDA cores; the last launch
+is one more tensor-core call. Inputs are seeded synthetic fields.
+"""
+from __future__ import annotations
+
+import argparse
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(prog="python -m paper_0911_2285_gb300.kernelbench")
+    sub = ap.add_subparsers(dest="what", required=True)
+    d = sub.add_parser("dhop")
+    d.add_argument("--workload", default="16^3x32")
+    d.add_argument("--k", type=int, default=8)
+    d.add_argument("--variants", type=int, nargs="+", default=[2, 4])
+    d.add_argument("--reps", type=int, default=5)
+    t = sub.add_parser("dots")
+    t.add_argument("--a", type=int, default=80)
+    t.add_argument("--b", type=int, default=8)
+    t.add_argument("--n", type=int, default=12 * 16 ** 3 * 32)
+    t.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args(argv)
+
+    import torch
+    from .lqcd import Solver, field_dots
+    if args.what == "dhop":
+        from seeded_inputs import WORKLOADS, workload_links
+        w = WORKLOADS[args.workload]
+        with Solver(workload_links(args.workload), w["dims"], w["kappa"], nev=2, m=8, n1=1, tol=1e-10,
+                    maxiter=100, precision="mixed", k_max=args.k) as s:
+            V = 1
+            for L in w["dims"]:
+                V *= L
+            alg = V * (4 * 48 + args.k * 4 * 96)
+            print(f"{args.workload}: autotuned shape {s.dslash_variant()}, algorithmic bytes {alg}")
+            for v in args.variants:
+                ms = s.time_kernel(10 + v, args.k, args.reps)
+                print(f"  shape {v}: {ms:.4f} ms  {alg / ms / 1e6:.0f} GB/s")
+            for v in args.variants:
+                s.time_kernel(10 + v, args.k, 1)
+    else:
+        g = torch.Generator(device="cuda").manual_seed(5)
+        X = torch.randn(args.a, args.n, dtype=torch.complex64, device="cuda", generator=g)
+        Y = torch.randn(args.b, args.n, dtype=torch.complex64, device="cuda", generator=g)
+        gb = (args.a + args.b) * args.n * 8 / 1e9
+        _, t1 = field_dots(X, Y, path=1, reps=args.reps)
+        _, t0 = field_dots(X, Y, path=0, reps=args.reps)
+        print(f"X^H Y {args.a}x{args.b}, n={args.n}: tensor cores {t1:.4f} ms ({gb / t1 * 1e3:.0f} GB/s), "
+              f"CUDA cores {t0:.4f} ms ({gb / t0 * 1e3:.0f} GB/s)")
+        field_dots(X, Y, path=1)
+
+
+if __name__ == "__main__":
+    main()
