@@ -221,12 +221,12 @@ long long lqcd_kernel_launches(void);
  * slot buffers hold, repeated reps times. kernel: 0 = operator pair
  * A p, A^+ phat (Krylov precision) with the fused sigma reduction; 1 = residual
  * update; 2 = direction update; 3 = FP64 true residual + reliable-update
- * replacement; 10 + v = operator pair in kernel shape v, 20 = the plane-
+ * replacement; 10 + v = operator pair in kernel shape v (v < 19), 99 = the plane-
  * streaming operator pair (see lqcd_dslash_variant). Leaves the slots idle. */
 lqcd_status lqcd_time_kernel(lqcd_ctx *ctx, int kernel, int k, int reps, double *avg_ms);
 
 /* Measurement hook: the operator-kernel shape the autotuner picked at init
- * (timing every shape on this lattice with a full batch): 0..9, or 100 for
+ * (timing every shape on this lattice with a full batch): 0..18, or 100 for
  * the plane-streaming kernel; -1 for NULL. */
 int lqcd_dslash_variant(const lqcd_ctx *ctx);
 

@@ -217,12 +217,15 @@ template <int NV, typename C> __device__ __forceinline__ void block_sum(C (&v)[N
 
 // "Last block done" handshake: every block calls this after publishing its
 // partials; returns true in exactly one block (the last to arrive), which then
-// sees all partials. counter must be zero before the launch; it is reset here.
+// sees all partials. The partials must be written by thread 0 of the block, or
+// fenced (__threadfence) by the thread that wrote them before this call; the
+// other threads' stores need no fence. counter must be zero before the launch;
+// it is reset here.
 __device__ __forceinline__ bool last_block(unsigned* counter, unsigned nblocks) {
     __shared__ bool am_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         unsigned prev = atomicAdd(counter, 1u);
         am_last = (prev == nblocks - 1);
         if (am_last) *counter = 0;   // ready for the next launch

@@ -289,11 +289,33 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
 //   PAIR = false: one thread per (site, operator) job, 2 jobs per slot;
 //   PAIR = true : one thread per (site, slot) computes both operators and
 //                 shares each link load between them.
-template <typename S, int THREADS, int MINB, bool PAIR>
+//   BZ > 0: a block covers an 8 x 8 x BZ brick of sites (THREADS = 64 BZ) instead
+//           of THREADS consecutive sites, so more y and z neighbours are L1 hits.
+template <int THREADS, int BZ> struct SiteMap {
+    int nunits;
+    __device__ __forceinline__ SiteMap(const Geom& g) {
+        nunits = BZ > 0 ? (g.L[0] / 8) * (g.L[1] / 8) * (g.L[2] / (BZ > 0 ? BZ : 1)) * g.L[3]
+                        : (g.V + THREADS - 1) / THREADS;
+    }
+    __device__ __forceinline__ int site(const Geom& g, int u) const {   // -1: none
+        if (BZ == 0) {
+            const int s = u * THREADS + (int)threadIdx.x;
+            return s < g.V ? s : -1;
+        }
+        const int nbx = g.L[0] / 8, nby = g.L[1] / 8, nbz = g.L[2] / (BZ > 0 ? BZ : 1);
+        const int bx = u % nbx, r1 = u / nbx, by = r1 % nby, r2 = r1 / nby, bz = r2 % nbz, t = r2 / nbz;
+        const int x = bx * 8 + (threadIdx.x & 7), y = by * 8 + ((threadIdx.x >> 3) & 7);
+        const int z = bz * BZ + (threadIdx.x >> 6);
+        return x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
+    }
+};
+
+template <typename S, int THREADS, int MINB, bool PAIR, int BZ = 0>
 __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const void* links, double kappa,
                                                                SlotState* states, const SlotPtrs* ptrs,
                                                                int njobs) {
     const int job = blockIdx.x % njobs, sblock = blockIdx.x / njobs, nsb = gridDim.x / njobs;
+    const SiteMap<THREADS, BZ> map(g);
     const int slot = PAIR ? job : job >> 1, which = PAIR ? 0 : job & 1;
     SlotState& st = states[slot];
     const SlotPtrs& P = ptrs[slot];
@@ -305,7 +327,9 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
     Acc<S> sacc;   // sigma, |phat|^2, |Ap|^2
     if (PAIR) {
         FieldIn<S> inp{P.p, g.V}, inh{P.phat, g.V};
-        for (int s = sblock * THREADS + threadIdx.x; s < g.V; s += nsb * THREADS) {
+        for (int u = sblock; u < map.nunits; u += nsb) {
+            const int s = map.site(g, u);
+            if (s < 0) continue;
             C a[12], b[12], self[12];
             hop_site_pair<S>(g, U, inp, inh, s, a, b);
             inp.load(s, self);
@@ -325,7 +349,9 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
     } else {
         FieldIn<S> in{which ? P.phat : P.p, g.V};
         void* out = which ? P.Ahp[par] : P.Ap[par];
-        for (int s = sblock * THREADS + threadIdx.x; s < g.V; s += nsb * THREADS) {
+        for (int u = sblock; u < map.nunits; u += nsb) {
+            const int s = map.site(g, u);
+            if (s < 0) continue;
             C acc[12], self[12];
             if (which) hop_site<true, S>(g, U, in, s, acc);
             else hop_site<false, S>(g, U, in, s, acc);
@@ -358,6 +384,91 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
             st.status = ST_BREAKDOWN;
         } else {
             st.alpha = cdiv(st.rho, st.sigma);
+        }
+    }
+}
+
+// Operator pair with one warp per (32-site group, job): a block holds the
+// jobs (slot, operator) of up to JPB/2 slots for the same sites, so the link
+// loads of one site group are shared through L1 by every job of the block.
+// Blocks loop over site groups (grid-stride, a fixed grid independent of the
+// number of slots, so each slot's sigma partition does not depend on the
+// batch). sigma: per-lane FP32 sums, warp sums, one FP64 partial per (block,
+// slot) in that slot's partial buffer; the last block of the launch (one
+// counter in slot 0) adds each slot's partials in block order.
+constexpr int GRP_BLOCKS = 4 * 152;   // blocks per job half (fixed)
+template <int JPB, int MINB>
+__global__ void __launch_bounds__(32 * JPB, MINB)
+    matvec_group_kernel(Geom g, const void* links, float kappa, SlotState* states, const SlotPtrs* ptrs,
+                        int nslots) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int njobs = 2 * nslots;
+    const int job = blockIdx.y * JPB + warp;
+    const int slot = job >> 1, which = job & 1;
+    const int ngroups = (g.V + 31) >> 5;
+    LinksF U{reinterpret_cast<const float4*>(links), g.V};
+    Acc<float> sacc;
+    if (job < njobs && states[slot].status == ST_RUNNING) {
+        const SlotState& st = states[slot];
+        const SlotPtrs& P = ptrs[slot];
+        const int par = st.iter & 1;
+        FieldIn<float> in{which ? P.phat : P.p, g.V};
+        void* out = which ? P.Ahp[par] : P.Ap[par];
+        for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+            const int s = (grp << 5) + lane;
+            if (s >= g.V) break;
+            float2 acc[12], self[12];
+            if (which) hop_site<true, float>(g, U, in, s, acc);
+            else hop_site<false, float>(g, U, in, s, acc);
+            in.load(s, self);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[c] = self[c] - kappa * acc[c];
+            Field<float>::store(out, g.V, s, acc);
+            if (!which) {
+                float2 ph[12];
+                Field<float>::load(P.phat, g.V, s, ph);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    sacc.z = sacc.z + cdot(ph[c], acc[c]);
+                    sacc.a += abs2(ph[c]);
+                    sacc.b += abs2(acc[c]);
+                }
+            }
+        }
+        if (!which) {
+            float2 z = warp_sum(sacc.z);
+            float2 ab = warp_sum(make_float2(sacc.a, sacc.b));
+            if (lane == 0) {
+                double2* pp = P.partials + (size_t)CNT_MATVEC * PARTIAL_STRIDE + (size_t)blockIdx.x * 2;
+                pp[0] = to_d(z);
+                pp[1] = to_d(ab);
+                __threadfence();
+            }
+        }
+    }
+    // one arrival per block; the last block finishes every slot
+    if (!last_block(ptrs[0].counters + CNT_GROUP, gridDim.x * gridDim.y)) return;
+    for (int sl = warp; sl < nslots; sl += JPB) {
+        SlotState& st = states[sl];
+        if (st.status != ST_RUNNING) continue;
+        const double2* pp = ptrs[sl].partials + (size_t)CNT_MATVEC * PARTIAL_STRIDE;
+        double2 z = make_double2(0.0, 0.0), ab = make_double2(0.0, 0.0);
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            z = z + __ldcg(pp + 2 * b);
+            ab = ab + __ldcg(pp + 2 * b + 1);
+        }
+        z = warp_sum(z);
+        ab = warp_sum(ab);
+        if (lane == 0) {
+            st.sigma = z;
+            st.phat_norm = sqrt(ab.x);
+            st.ap_norm = sqrt(ab.y);
+            st.matvecs += 2;
+            if (!(cabs_(st.sigma) >= BREAK_TOL * st.phat_norm * st.ap_norm) || cabs2(st.sigma) == 0.0) {
+                st.status = ST_BREAKDOWN;
+            } else {
+                st.alpha = cdiv(st.rho, st.sigma);
+            }
         }
     }
 }
@@ -869,16 +980,33 @@ cudaError_t launch_bicg_start(const Geom& g, const void* links64, double kappa, 
     return cudaGetLastError();
 }
 
-template <typename S, int THREADS, int MINB, bool PAIR>
+// SPT: sites per thread (grid-stride), which amortises each block's set-up and
+// reduction tail over more sites.
+template <typename S, int THREADS, int MINB, bool PAIR, int BZ = 0, int SPT = 1>
 static void matvec_launch(const Geom& g, const void* links, double kappa, SlotState* states, const SlotPtrs* ptrs,
                           int nslots, cudaStream_t s) {
     const int njobs = PAIR ? nslots : 2 * nslots;
-    int nb = div_up((size_t)g.V, THREADS);
+    int nb = div_up((size_t)g.V, (size_t)THREADS * SPT);
     if (nb > PARTIAL_STRIDE / 2) nb = PARTIAL_STRIDE / 2;
-    matvec_kernel<S, THREADS, MINB, PAIR><<<nb * njobs, THREADS, 0, s>>>(g, links, kappa, states, ptrs, njobs);
+    matvec_kernel<S, THREADS, MINB, PAIR, BZ><<<nb * njobs, THREADS, 0, s>>>(g, links, kappa, states, ptrs, njobs);
+}
+// The brick shapes need Lx, Ly multiples of 8 and Lz a multiple of BZ.
+static bool brick_ok(const Geom& g, int bz) { return g.L[0] % 8 == 0 && g.L[1] % 8 == 0 && g.L[2] % bz == 0; }
+
+template <int JPB, int MINB>
+static void matvec_group_launch(const Geom& g, const void* links, double kappa, SlotState* states,
+                                const SlotPtrs* ptrs, int nslots, cudaStream_t s) {
+    const int njobs = 2 * nslots;
+    dim3 grid(GRP_BLOCKS, (njobs + JPB - 1) / JPB);
+    matvec_group_kernel<JPB, MINB><<<grid, 32 * JPB, 0, s>>>(g, links, (float)kappa, states, ptrs, nslots);
 }
 
-int matvec_variants() { return 10; }
+int matvec_variants() { return 19; }
+bool matvec_variant_ok(const Geom& g, int v) {
+    if (v == 13 || v == 14) return brick_ok(g, 4);
+    if (v == 15) return brick_ok(g, 2);
+    return v >= 0 && v < 19;
+}
 
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
                                const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant) {
@@ -895,6 +1023,15 @@ cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, i
             case 7: matvec_launch<float, 128, 3, true>(g, links, kappa, states, ptrs, nslots, s); break;
             case 8: matvec_launch<float, 256, 2, true>(g, links, kappa, states, ptrs, nslots, s); break;
             case 9: matvec_launch<float, 64, 8, false>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 10: matvec_group_launch<8, 3>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 11: matvec_group_launch<8, 2>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 12: matvec_group_launch<16, 1>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 13: matvec_launch<float, 256, 3, false, 4>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 14: matvec_launch<float, 256, 2, true, 4>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 15: matvec_launch<float, 128, 4, true, 2>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 16: matvec_launch<float, 256, 3, false, 0, 4>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 17: matvec_launch<float, 128, 4, true, 0, 4>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 18: matvec_launch<float, 256, 2, true, 0, 2>(g, links, kappa, states, ptrs, nslots, s); break;
             default: matvec_launch<float, 128, 1, false>(g, links, kappa, states, ptrs, nslots, s); break;
         }
     }

@@ -80,6 +80,8 @@ cudaError_t launch_matvec_tiled(const Geom& g, const TileGeom& tg, const void* l
 
 // variant: operator-kernel shape chosen by the autotuner (0 .. matvec_variants()-1)
 int matvec_variants();
+// false when shape v cannot run on this lattice (brick shapes need Lx, Ly % 8 == 0, Lz % BZ == 0)
+bool matvec_variant_ok(const Geom& g, int v);
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec,
                                SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant);
 cudaError_t launch_bicg_update(int prec, SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);

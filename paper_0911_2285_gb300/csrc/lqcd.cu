@@ -1141,10 +1141,14 @@ extern "C" lqcd_status lqcd_restart_coefficients(int m, int nev, const double* H
 // ============================================================ measurement
 extern "C" long long lqcd_kernel_launches(void) { return launches_so_far(); }
 
+constexpr int TIME_TILED = 99;   // lqcd_time_kernel id of the plane-streaming shape
+
 static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, double* avg_ms) {
     if (!c || !avg_ms || k < 1 || k > c->kmax || reps < 1) return LQCD_ERR_ARG;
-    if (kernel < 0 || (kernel > 3 && kernel < 10) || (kernel >= 10 + matvec_variants() && kernel != 20)) return LQCD_ERR_ARG;
-    if (kernel == 20 && !c->tile_ok[k]) return LQCD_ERR_ARG;
+    if (kernel < 0 || (kernel > 3 && kernel < 10) || (kernel >= 10 + matvec_variants() && kernel != TIME_TILED))
+        return LQCD_ERR_ARG;
+    if (kernel == TIME_TILED && !c->tile_ok[k]) return LQCD_ERR_ARG;
+    if (kernel >= 10 && kernel < 10 + matvec_variants() && !matvec_variant_ok(c->g, kernel - 10)) return LQCD_ERR_ARG;
     // Slots 0..k-1 iterate with fixed scalars on whatever their buffers hold.
     std::vector<SlotState> tmpl(c->kmax);
     for (int s = 0; s < c->kmax; ++s) {
@@ -1170,7 +1174,7 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
         CK(cudaEventRecord(e0, c->stream));
         if (kernel == 0) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->stream,
                                                c->dslash_variant));
-        else if (kernel == 20) CK(launch_matvec(c, k, TILED));
+        else if (kernel == TIME_TILED) CK(launch_matvec(c, k, TILED));
         else if (kernel >= 10) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k,
                                                      c->stream, kernel - 10));
         else if (kernel == 1) CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
@@ -1207,6 +1211,7 @@ static lqcd_status autotune(lqcd_ctx* c) {
     double best = 1e300;
     for (int v = 0; v < nv; ++v) {
         double ms = 0.0;
+        if (!matvec_variant_ok(c->g, v)) { c->tune_ms[v] = -1.0; continue; }
         lqcd_status s = time_kernel_impl(c, 10 + v, c->kmax, 1, &ms);   // warm-up
         if (s != LQCD_OK) return s;
         s = time_kernel_impl(c, 10 + v, c->kmax, 3, &ms);
@@ -1216,9 +1221,9 @@ static lqcd_status autotune(lqcd_ctx* c) {
     }
     if (c->tile_ok[c->kmax]) {
         double ms = 0.0;
-        lqcd_status s = time_kernel_impl(c, 20, c->kmax, 1, &ms);
+        lqcd_status s = time_kernel_impl(c, TIME_TILED, c->kmax, 1, &ms);
         if (s != LQCD_OK) return s;
-        s = time_kernel_impl(c, 20, c->kmax, 3, &ms);
+        s = time_kernel_impl(c, TIME_TILED, c->kmax, 3, &ms);
         if (s != LQCD_OK) return s;
         c->tune_ms.push_back(ms);
         if (ms < best) { best = ms; c->dslash_variant = TILED; }
@@ -1241,7 +1246,8 @@ extern "C" lqcd_status lqcd_apply_pair(lqcd_ctx* c, int variant, int k, const do
     if (!c || !p || !phat || !Ap || !Ahp || k < 1 || k > c->kmax) return LQCD_ERR_ARG;
     if (variant == TILED) {
         if (!c->tile_ok[k]) return LQCD_ERR_ARG;
-    } else if (variant < 0 || variant >= matvec_variants() || (!c->kprec && variant != 0)) {
+    } else if (variant < 0 || variant >= matvec_variants() || (!c->kprec && variant != 0) ||
+               !matvec_variant_ok(c->g, variant)) {
         return LQCD_ERR_ARG;
     }
     const size_t fb = 2 * c->N;   // doubles per host field

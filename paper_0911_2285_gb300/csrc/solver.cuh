@@ -64,7 +64,7 @@ struct SlotPtrs {
 };
 
 enum CounterId { CNT_MATVEC = 0, CNT_UPDATE = 1, CNT_RU = 2, CNT_REPLACE = 3, CNT_START = 4,
-                 CNT_GEMM_V = 5, CNT_GEMM_W = 6, CNT_COUNT = 8 };
+                 CNT_GEMM_V = 5, CNT_GEMM_W = 6, CNT_GROUP = 7, CNT_COUNT = 8 };
 
 // Slot of the current residual r_{j-1} at the start of an iteration.
 __device__ __forceinline__ int cur_slot(const SlotState& st) { return st.m > 0 ? st.vs : 0; }
