@@ -225,6 +225,15 @@ long long lqcd_kernel_launches(void);
  * streaming operator pair (see lqcd_dslash_variant). Leaves the slots idle. */
 lqcd_status lqcd_time_kernel(lqcd_ctx *ctx, int kernel, int k, int reps, double *avg_ms);
 
+/* Implementation switch (no counterpart in the paper): on != 0 (the default)
+ * runs the FP32 Galerkin projections (U_l^H r, growth blocks) and the FP32
+ * restart window product V <- V Yc, W <- W Zc on the tensor cores (3xTF32
+ * tcgen05 MMAs) where the shapes allow (m <= 64, 2 nev <= 24, 12 V a multiple
+ * of 128); on = 0 uses the CUDA-core kernels. Results agree to FP32 rounding,
+ * not bit for bit. Waits for the context's stream; LQCD_ERR_STATE while
+ * serving requests are in flight. */
+lqcd_status lqcd_set_tensor_cores(lqcd_ctx *ctx, int on);
+
 /* Measurement hook: the operator-kernel shape the autotuner picked at init
  * (timing every shape on this lattice with a full batch): 0..18, or 100 for
  * the plane-streaming kernel; -1 for NULL. */

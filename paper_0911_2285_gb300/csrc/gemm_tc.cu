@@ -12,8 +12,10 @@
 //
 // Precision: 3xTF32. Each operand v is split into big = tf32(v) and
 // small = v - big, and the tile product is big.big + big.small + small.big,
-// which keeps FP32-level accuracy. Each run of TC_FLUSH K-tiles accumulates in
-// tensor memory (FP32); the runs and the CTAs (split-K) are summed in FP64.
+// which keeps FP32-level accuracy. The tensor core truncates as it
+// accumulates, so big.big and the corrections accumulate in separate
+// tensor-memory columns over short runs (TC_FLUSH K-tiles, 8 MMAs each); the
+// runs and the CTAs (split-K) are summed in FP64.
 //
 // Data movement: TMA tensor copies with 128-byte swizzle bring 32-real K-tiles
 // of X (128 rows) and Y (8 rows) into a 4-stage shared-memory ring; the split
@@ -39,10 +41,12 @@ constexpr int TC_KT = 32;        // reals per row per K-tile (128 bytes)
 constexpr int TC_M = 128;        // X rows per CTA tile
 constexpr int TC_NB = 8;         // Y fields per launch (N = 2 * TC_NB)
 constexpr int TC_STAGES = 5;
-constexpr int TC_FLUSH = 16;     // K-tiles per FP32 accumulation run in tensor memory
+constexpr int TC_FLUSH = 2;      // K-tiles per FP32 accumulation run in tensor memory
 constexpr int TC_XW = 8;         // split (transform) warps
 constexpr int TC_THREADS = 32 * (2 + TC_XW);
-constexpr unsigned TC_TMEM_COLS = 32;   // two accumulators of 16 columns
+constexpr int TC_NBUF = 4;       // accumulator sets in flight (runs the readers may lag behind)
+constexpr int TC_SUPER = 16;     // runs summed in FP32 before an FP64 add
+constexpr unsigned TC_TMEM_COLS = 128;  // TC_NBUF runs x (big.big, correction) x 16 columns
 
 struct __align__(1024) TcStage {
     float xa[TC_M * TC_KT];      // TMA X tile, then its TF32 big part in place
@@ -52,7 +56,7 @@ struct __align__(1024) TcStage {
 };
 static_assert(sizeof(TcStage) % 1024 == 0, "stage must keep 1024-byte alignment");
 struct TcBars {
-    uint64_t full[TC_STAGES], ready[TC_STAGES], empty[TC_STAGES], accfull[2], accempty[2];
+    uint64_t full[TC_STAGES], ready[TC_STAGES], empty[TC_STAGES], accfull[TC_NBUF], accempty[TC_NBUF];
     unsigned tmem;
     int abort;
 };
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&B->ready[s], TC_XW);
             mbar_init(&B->empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) { mbar_init(&B->accfull[b], 1); mbar_init(&B->accempty[b], 4); }
+        for (int b = 0; b < TC_NBUF; ++b) { mbar_init(&B->accfull[b], 1); mbar_init(&B->accempty[b], 4); }
         B->abort = 0;
         mbar_init_fence();
     }
@@ -149,21 +153,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {   // ---------------- MMA issuer
             int i = 0;
             for (; i < n; ++i) {
-                const int s = i % TC_STAGES, g = i / TC_FLUSH, b = g & 1;
-                if (i % TC_FLUSH == 0 && g >= 2 &&
-                    !wait_or_abort(&B->accempty[b], (unsigned)(g / 2 - 1) & 1u, abort))
+                const int s = i % TC_STAGES, g = i / TC_FLUSH, b = g % TC_NBUF;
+                if (i % TC_FLUSH == 0 && g >= TC_NBUF &&
+                    !wait_or_abort(&B->accempty[b], (unsigned)(g / TC_NBUF - 1) & 1u, abort))
                     break;
                 if (!wait_or_abort(&B->ready[s], (unsigned)(i / TC_STAGES) & 1u, abort)) break;
                 tc_fence_after();
                 TcStage& S = st[s];
-                const unsigned d = tmem + (unsigned)(b * 16);
+                // big.big and the two correction products go to separate accumulators
+                // (the tensor core truncates as it accumulates: keeping the small
+                // terms apart and the runs short keeps the sum at FP32 accuracy)
+                const unsigned dm = tmem + (unsigned)(b * 32), dc = dm + 16;
 #pragma unroll
                 for (int kk = 0; kk < TC_KT / 8; ++kk) {   // K = 8 reals (32 bytes) per MMA
                     const uint64_t ab = sdesc_k128(S.xa + 8 * kk), as = sdesc_k128(S.xs + 8 * kk);
                     const uint64_t bb = sdesc_k128(S.yb + 8 * kk), bs = sdesc_k128(S.ys + 8 * kk);
-                    mma_tf32(d, ab, bb, IDESC, (i % TC_FLUSH != 0 || kk > 0) ? 1u : 0u);
-                    mma_tf32(d, ab, bs, IDESC, 1u);
-                    mma_tf32(d, as, bb, IDESC, 1u);
+                    const unsigned keep = (i % TC_FLUSH != 0 || kk > 0) ? 1u : 0u;
+                    mma_tf32(dm, ab, bb, IDESC, keep);
+                    mma_tf32(dc, ab, bs, IDESC, keep);
+                    mma_tf32(dc, as, bb, IDESC, 1u);
                 }
                 mma_commit(&B->empty[s]);
                 if (i % TC_FLUSH == TC_FLUSH - 1 || i == n - 1) mma_commit(&B->accfull[b]);
@@ -176,18 +184,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const bool reader = warp < 6;
         const unsigned lane_base = (unsigned)((warp & 3) * 32) << 16;
         int next_group = 0;
+        float sum32[16];   // FP32 sum of up to TC_SUPER runs (FP64 adds are slow on this GPU)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) sum32[c] = 0.f;
         auto read_group = [&](int g) -> bool {
+            const int b = g % TC_NBUF;
             // warp-uniform outcome: tcgen05.ld below needs the whole warp
-            if (!__all_sync(0xffffffffu, wait_or_abort(&B->accfull[g & 1], (unsigned)(g / 2) & 1u, abort)))
+            if (!__all_sync(0xffffffffu, wait_or_abort(&B->accfull[b], (unsigned)(g / TC_NBUF) & 1u, abort)))
                 return false;
             tc_fence_after();
-            float v[16];
-            tmem_ld16(tmem + lane_base + (unsigned)((g & 1) * 16), v);
-#pragma unroll
-            for (int c = 0; c < 16; ++c) acc[c] += (double)v[c];
+            float v[16], w[16];
+            tmem_ld16(tmem + lane_base + (unsigned)(b * 32), v);
+            tmem_ld16(tmem + lane_base + (unsigned)(b * 32 + 16), w);
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&B->accempty[g & 1]);
+            if (lane == 0) mbar_arrive(&B->accempty[b]);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) sum32[c] += v[c] + w[c];
+            if (g % TC_SUPER == TC_SUPER - 1 || g == ngroups - 1) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    acc[c] += (double)sum32[c];
+                    sum32[c] = 0.f;
+                }
+            }
             return true;
         };
         bool ok = true;
@@ -221,7 +241,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(&B->ready[s]);
-            if (reader && i % TC_FLUSH == 1 && i > TC_FLUSH) ok = read_group(next_group++);
+            // run g is read TC_NBUF - 2 runs after it was issued
+            if (reader && i % TC_FLUSH == 1 && i > (TC_NBUF - 1) * TC_FLUSH) ok = read_group(next_group++);
         }
         if (reader)
             while (ok && next_group < ngroups) ok = read_group(next_group++);
@@ -256,6 +277,273 @@ __global__ void dots_tc_reduce_kernel(int a, int b, int nblk, const double* part
     }
     if (conj_store) Cm[(size_t)j * ldc + i] = make_double2(re, -im);
     else Cm[(size_t)i * ldc + j] = make_double2(re, im);
+}
+
+// ------------------------------------------------------------------------
+// In-place window product of the BiCG-eigen restart on the tensor cores
+// (Alg. BiCG-eigen: V <- V Yc, W <- W Zc, FP32 windows), one job per
+// (slot, side):
+//   new slot k = sum_{i<m} s_i c_ik old slot i   (k < r),   new slot r = old slot m,
+// plus the coupling dots of the new vectors with (A p - beta q) or
+// (A^+ phat - conj(beta) s), and the new H row/column (same contract as the
+// CUDA-core window_gemm_kernel).
+//
+// Real form per element e: y(e)[2k + c'] = sum_{i, c} x(e)[2i + c] B[2k + c'][2i + c]
+// with the 2 x 2 blocks B = [[cr, -ci], [ci, cr]] of s_i c_ik: an MMA with
+// M = 128 elements, N = 2 r (padded to 48), K = 2 m reals in K-chunks of 16
+// fields. The fields are element-contiguous, so 1-D bulk copies bring 16
+// field rows of 128 elements into a raw stage and eight warps transpose them
+// into the 128-byte-swizzled K-major operand (3xTF32 split on the way).
+// Roles: warp 0 copies, warp 1 issues MMAs, warps 2-9 transpose, warps 10-13
+// (one per tensor-memory lane quarter) drain the two alternating accumulators
+// and store, copy slot m and form the coupling dots.
+constexpr int RT_E = 128;        // elements per tile
+constexpr int RT_KF = 16;        // fields per K-chunk (32 reals, one 128-byte row)
+constexpr int RT_QMAX = 4;       // K-chunks: m <= 64
+constexpr int RT_RMAX = 24;      // kept vectors r <= 24
+constexpr int RT_N = 2 * RT_RMAX;
+constexpr int RT_STAGES = 3;
+constexpr int RT_XW = 8;         // transpose warps
+constexpr int RT_EW = 4;         // epilogue warps
+constexpr int RT_THREADS = 32 * (2 + RT_XW + RT_EW);
+constexpr unsigned RT_TMEM_COLS = 512;   // two tiles x (one big.big accumulator per K-chunk + corrections)
+constexpr int RT_ACC_STRIDE = 256;       // columns per tile accumulator set: 4 x 48 main + 48 correction
+
+struct __align__(1024) RtSmem {
+    float bb[RT_QMAX][RT_N * 32];    // coefficients, big part (K-major, swizzled), per K-chunk
+    float bs[RT_QMAX][RT_N * 32];    // small part
+    float ab[2][RT_E * 32];          // transposed X chunk, big part (two buffers)
+    float as[2][RT_E * 32];          // small part
+    float raw[RT_STAGES][RT_KF * RT_E * 2];   // field rows as copied: [field][element][re, im]
+    uint64_t raw_full[RT_STAGES], raw_empty[RT_STAGES], a_full[2], a_empty[2], acc_full[2], acc_empty[2];
+    double2 dots[RT_EW][RT_RMAX];
+    unsigned tmem;
+    int abort;
+};
+constexpr size_t RT_SMEM = sizeof(RtSmem) + 1024;
+
+// byte offset of the 16-byte granule j of row n in a 128-byte-swizzled K-major tile
+__device__ __forceinline__ int sw128(int n, int j) { return n * 128 + ((j ^ (n & 7)) << 4); }
+
+__global__ void __launch_bounds__(RT_THREADS, 1)
+    restart_tc_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N, int* err) {
+    const int slot = blockIdx.y >> 1, side = blockIdx.y & 1;
+    SlotState& st = states[slot];
+    const SlotPtrs& P = ptrs[slot];
+    if (st.status != ST_RUNNING || st.restart_r == 0) return;   // uniform over the CTA
+    extern __shared__ unsigned char smem_raw[];
+    RtSmem* S = reinterpret_cast<RtSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    volatile int* abort = &S->abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = st.m, r = st.restart_r, ldc = 2 * st.nev + 1;
+    const int Q = (m + RT_KF - 1) / RT_KF;
+    const int par = st.iter & 1;
+    char* base = reinterpret_cast<char*>(side ? P.W : P.V);
+    const size_t fbytes = N * 8;
+    const long long tiles = (long long)(N / RT_E);
+    const long long t0 = (long long)blockIdx.x * tiles / gridDim.x;
+    const long long t1 = (long long)(blockIdx.x + 1) * tiles / gridDim.x;
+    const int nt = (int)(t1 - t0);
+    const int nchunks = nt * Q;
+
+    if (tid == 0) {
+        for (int s = 0; s < RT_STAGES; ++s) { mbar_init(&S->raw_full[s], 1); mbar_init(&S->raw_empty[s], RT_XW); }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&S->a_full[b], RT_XW);
+            mbar_init(&S->a_empty[b], 1);
+            mbar_init(&S->acc_full[b], 1);
+            mbar_init(&S->acc_empty[b], RT_EW);
+        }
+        S->abort = 0;
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        __syncwarp();
+        tmem_alloc(&S->tmem, RT_TMEM_COLS);
+        tmem_relinquish();
+    }
+    // coefficient operand: row n = 2k + c', K index 2i + c, blocks [[cr, -ci], [ci, cr]] of s_i c_ik
+    {
+        const double2* coef = side ? P.coefZ : P.coefY;
+        for (int w = tid; w < RT_QMAX * RT_N * 8; w += RT_THREADS) {
+            const int q = w / (RT_N * 8), n = (w / 8) % RT_N, j = w % 8;
+            const int k = n >> 1, co = n & 1;
+            float v[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = q * RT_KF + 2 * j + h;
+                double2 c = make_double2(0.0, 0.0);
+                if (k < r && i < m) {
+                    const double2 sc = side ? P.wscale[i] : make_double2(P.vscale[i], 0.0);
+                    c = sc * coef[i * ldc + k];
+                }
+                v[2 * h] = co ? (float)c.y : (float)c.x;
+                v[2 * h + 1] = co ? (float)c.x : -(float)c.y;
+            }
+            float4 big, small;
+            split4(make_float4(v[0], v[1], v[2], v[3]), big, small);
+            *reinterpret_cast<float4*>(reinterpret_cast<char*>(S->bb[q]) + sw128(n, j)) = big;
+            *reinterpret_cast<float4*>(reinterpret_cast<char*>(S->bs[q]) + sw128(n, j)) = small;
+        }
+        fence_proxy_async();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = S->tmem;
+    constexpr unsigned IDESC = idesc_tf32(RT_E, RT_N);
+
+    if (warp == 0) {
+        if (lane == 0) {   // ------------------------------ copies
+            int g = 0;
+            for (; g < nchunks; ++g) {
+                const int s = g % RT_STAGES, q = g % Q;
+                const long long e0 = (t0 + g / Q) * RT_E;
+                if (g >= RT_STAGES &&
+                    !wait_or_abort(&S->raw_empty[s], (unsigned)(g / RT_STAGES - 1) & 1u, abort))
+                    break;
+                const int nf = min(RT_KF, m - q * RT_KF);
+                mbar_arrive_expect_tx(&S->raw_full[s], (unsigned)nf * RT_E * 8);
+                for (int f = 0; f < nf; ++f)
+                    bulk_copy_g2s(S->raw[s] + f * RT_E * 2, base + (size_t)(q * RT_KF + f) * fbytes + e0 * 8,
+                                  RT_E * 8, &S->raw_full[s]);
+            }
+            for (int h = g - RT_STAGES > 0 ? g - RT_STAGES : 0; h < g; ++h)
+                mbar_wait(&S->raw_full[h % RT_STAGES], (unsigned)(h / RT_STAGES) & 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ------------------------------ MMAs
+            int g = 0;
+            for (; g < nchunks; ++g) {
+                const int t = g / Q, q = g % Q, b = g & 1, acc = t & 1;
+                if (q == 0 && t >= 2 &&
+                    !wait_or_abort(&S->acc_empty[acc], (unsigned)(t / 2 - 1) & 1u, abort))
+                    break;
+                if (!wait_or_abort(&S->a_full[b], (unsigned)(g / 2) & 1u, abort)) break;
+                tc_fence_after();
+                // big.big of each K-chunk in its own accumulator, all corrections in one:
+                // the tensor core truncates as it accumulates, so short sums of
+                // like-sized terms keep the product at FP32 accuracy
+                const unsigned dm = tmem + (unsigned)(acc * RT_ACC_STRIDE + q * RT_N);
+                const unsigned dc = tmem + (unsigned)(acc * RT_ACC_STRIDE + RT_QMAX * RT_N);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t ab = sdesc_k128(S->ab[b] + 8 * kk), as = sdesc_k128(S->as[b] + 8 * kk);
+                    const uint64_t bb = sdesc_k128(S->bb[q] + 8 * kk), bs = sdesc_k128(S->bs[q] + 8 * kk);
+                    mma_tf32(dm, ab, bb, IDESC, kk > 0 ? 1u : 0u);
+                    mma_tf32(dc, ab, bs, IDESC, (q > 0 || kk > 0) ? 1u : 0u);
+                    mma_tf32(dc, as, bb, IDESC, 1u);
+                }
+                mma_commit(&S->a_empty[b]);
+                if (q == Q - 1) mma_commit(&S->acc_full[acc]);
+            }
+            if (g > 0) mbar_wait(&S->a_empty[(g - 1) & 1], (unsigned)((g - 1) / 2) & 1u);
+        }
+    } else if (warp < 2 + RT_XW) {   // ------------------- transpose + 3xTF32 split
+        const int xt = tid - 64;
+        for (int g = 0; g < nchunks; ++g) {
+            const int s = g % RT_STAGES, q = g % Q, b = g & 1;
+            bool ok = wait_or_abort(&S->raw_full[s], (unsigned)(g / RT_STAGES) & 1u, abort);
+            if (ok && g >= 2) ok = wait_or_abort(&S->a_empty[b], (unsigned)(g / 2 - 1) & 1u, abort);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const float2* raw = reinterpret_cast<const float2*>(S->raw[s]);
+            const int nf = min(RT_KF, m - q * RT_KF);
+#pragma unroll
+            for (int w = 0; w < RT_E * 8 / (32 * RT_XW); ++w) {
+                const int item = w * 32 * RT_XW + xt;       // (element e, granule j): e fastest
+                const int e = item % RT_E, j = item / RT_E;
+                const float2 x0 = 2 * j < nf ? raw[(2 * j) * RT_E + e] : make_float2(0.f, 0.f);
+                const float2 x1 = 2 * j + 1 < nf ? raw[(2 * j + 1) * RT_E + e] : make_float2(0.f, 0.f);
+                float4 big, small;
+                split4(make_float4(x0.x, x0.y, x1.x, x1.y), big, small);
+                *reinterpret_cast<float4*>(reinterpret_cast<char*>(S->ab[b]) + sw128(e, j)) = big;
+                *reinterpret_cast<float4*>(reinterpret_cast<char*>(S->as[b]) + sw128(e, j)) = small;
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&S->a_full[b]);
+                mbar_arrive(&S->raw_empty[s]);
+            }
+        }
+    } else {   // ------------------------------------------- epilogue
+        const int quarter = warp & 3, e = quarter * 32 + lane;
+        const unsigned lane_base = (unsigned)(quarter * 32) << 16;
+        const float2 bp = to_f(side ? st.beta_prev : conj_(st.beta_prev));
+        const char* cur = reinterpret_cast<const char*>(side ? P.Ap[par] : P.Ahp[par]);
+        const char* prv = reinterpret_cast<const char*>(side ? P.Ap[par ^ 1] : P.Ahp[par ^ 1]);
+        float2 dot[RT_RMAX];
+#pragma unroll
+        for (int k = 0; k < RT_RMAX; ++k) dot[k] = make_float2(0.f, 0.f);
+        for (int t = 0; t < nt; ++t) {
+            const int acc = t & 1;
+            if (!__all_sync(0xffffffffu, wait_or_abort(&S->acc_full[acc], (unsigned)(t / 2) & 1u, abort))) break;
+            tc_fence_after();
+            float y[RT_N];
+            const unsigned ta = tmem + lane_base + (unsigned)(acc * RT_ACC_STRIDE);
+#pragma unroll
+            for (int h = 0; h < RT_N / 16; ++h)   // corrections first, then each chunk's main sum
+                tmem_ld16(ta + (unsigned)(RT_QMAX * RT_N + 16 * h), *reinterpret_cast<float(*)[16]>(y + 16 * h));
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int h = 0; h < RT_N / 16; ++h) {
+                    float v[16];
+                    tmem_ld16(ta + (unsigned)(q * RT_N + 16 * h), v);
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) y[16 * h + c] += v[c];
+                }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S->acc_empty[acc]);
+            const size_t el = (size_t)(t0 + t) * RT_E + e;
+            const float2 c = reinterpret_cast<const float2*>(cur)[el];
+            const float2 pv = reinterpret_cast<const float2*>(prv)[el];
+            const float2 cv = c - bp * pv;
+            const float2 last = reinterpret_cast<const float2*>(base + (size_t)m * fbytes)[el];
+#pragma unroll
+            for (int k = 0; k < RT_RMAX; ++k)
+                if (k < r) {
+                    const float2 o = make_float2(y[2 * k], y[2 * k + 1]);
+                    reinterpret_cast<float2*>(base + (size_t)k * fbytes)[el] = o;
+                    dot[k] = dot[k] + (side ? cdot(o, cv) : cdot(cv, o));
+                }
+            reinterpret_cast<float2*>(base + (size_t)r * fbytes)[el] = last;
+        }
+#pragma unroll
+        for (int k = 0; k < RT_RMAX; ++k) {
+            const float2 d = warp_sum(dot[k]);
+            if (lane == 0) S->dots[quarter][k] = to_d(d);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, RT_TMEM_COLS);
+    }
+    // per-CTA partials of the coupling dots, then the last CTA of this (slot, side)
+    const int kind = side ? CNT_GEMM_W : CNT_GEMM_V;
+    double2* pp = P.partials + (size_t)kind * PARTIAL_STRIDE;
+    if (tid < RT_RMAX) {
+        double2 a = make_double2(0.0, 0.0);
+        for (int q = 0; q < RT_EW; ++q) a = a + S->dots[q][tid];
+        pp[(size_t)blockIdx.x * RT_RMAX + tid] = a;
+        __threadfence();
+    }
+    if (tid == 0 && *abort) atomicExch(err, 1);
+    if (!last_block(P.counters + kind, gridDim.x)) return;
+    if (tid < r) {
+        double2 tot = make_double2(0.0, 0.0);
+        for (unsigned b = 0; b < gridDim.x; ++b) tot = tot + __ldcg(pp + (size_t)b * RT_RMAX + tid);
+        if (side) {
+            P.H[tid * m + r] = (1.0 / st.rnorm) * tot;
+            P.wscale[tid] = make_double2(1.0, 0.0);
+        } else {
+            P.H[r * m + tid] = cdiv(make_double2(st.rnorm, 0.0), st.rho) * tot;
+            P.vscale[tid] = 1.0;
+        }
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -312,8 +600,35 @@ cudaError_t prepare_dots_tc() {
     std::call_once(g_prepare_once, [] {
         g_prepare_err = cudaFuncSetAttribute((const void*)dots_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)TC_SMEM);
+        if (g_prepare_err == cudaSuccess)
+            g_prepare_err = cudaFuncSetAttribute((const void*)restart_tc_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM);
     });
     return g_prepare_err;
+}
+
+bool restart_tc_supported(int m, int two_nev, size_t N) {
+    return m <= RT_QMAX * RT_KF && two_nev <= RT_RMAX && N % RT_E == 0 && N / RT_E >= 1;
+}
+
+cudaError_t launch_restart_tc(SlotState* states, const SlotPtrs* ptrs, int nslots, size_t N, int* err,
+                              cudaStream_t st) {
+    cudaError_t e = prepare_dots_tc();
+    if (e != cudaSuccess) return e;
+    if (!err) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_tc_err);
+        if (e != cudaSuccess) return e;
+        err = reinterpret_cast<int*>(p);
+    }
+    long long tiles = (long long)(N / RT_E);
+    int nblk = (2 * num_sms()) / (2 * nslots);
+    if (nblk < 1) nblk = 1;
+    if (nblk > tiles) nblk = (int)tiles;
+    if (nblk * RT_RMAX > PARTIAL_STRIDE) nblk = PARTIAL_STRIDE / RT_RMAX;
+    restart_tc_kernel<<<dim3(nblk, 2 * nslots), RT_THREADS, RT_SMEM, st>>>(states, ptrs, N, err);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 // FP32 fields only: X = a fields, Y = b fields, each N complex, consecutive

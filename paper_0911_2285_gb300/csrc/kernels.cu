@@ -245,6 +245,8 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
     SlotState& st = states[blockIdx.y];
     const SlotPtrs& P = ptrs[blockIdx.y];
     if (st.status != ST_RUNNING) return;
+    if (st.m > 0 && blockIdx.x == 0)   // a fresh window: H is tridiagonal until the first restart
+        for (int e = threadIdx.x; e < st.m * st.m; e += blockDim.x) P.H[e] = make_double2(0.0, 0.0);
     using C = cplx<S>;
     Acc<S> acc;   // rho, |r|^2, |b|^2
     const size_t units = N / 2;
@@ -894,14 +896,11 @@ cudaError_t launch_convert(const void* src, int sp, void* dst, int dp, size_t n,
     return cudaGetLastError();
 }
 
-static int g_dots_path = 1;   // 1: tensor cores for FP32 x FP32 when the shape allows
-void set_dots_path(int path) { g_dots_path = path; }
-
 cudaError_t launch_multidot(int a, const void* X, int xp, int b, const void* Y, int yp, size_t N, double2* Cm,
                             int ldc, int conj_store, double2* scratch, size_t scratch_elems, cudaStream_t st,
-                            int* err) {
+                            int* err, int tensor_cores) {
     if (a <= 0 || b <= 0) return cudaSuccess;
-    if (g_dots_path == 1 && xp == 1 && yp == 1 && dots_tc_supported(a, X, Y, N) &&
+    if (tensor_cores && xp == 1 && yp == 1 && dots_tc_supported(a, X, Y, N) &&
         dots_tc_scratch_doubles(a) <= 2 * scratch_elems)
         return launch_dots_tc(a, X, N * 8, b, Y, N * 8, N, Cm, ldc, conj_store, reinterpret_cast<double*>(scratch),
                               2 * scratch_elems, err, st);

@@ -39,14 +39,18 @@ cudaError_t launch_convert(const void* src, int src_prec, void* dst, int dst_pre
 // conj_store: store conj(C) transposed, C[j*ldc + i] instead.
 cudaError_t launch_multidot(int a, const void* X, int xprec, int b, const void* Y, int yprec,
                             size_t N, double2* C, int ldc, int conj_store, double2* scratch,
-                            size_t scratch_elems, cudaStream_t st, int* err = nullptr);
-// 1 (default): FP32 x FP32 products go to the tensor-core path where it applies; 0: CUDA cores.
-void set_dots_path(int path);
+                            size_t scratch_elems, cudaStream_t st, int* err = nullptr, int tensor_cores = 1);
+// tensor_cores = 1: FP32 x FP32 products go to the tensor-core path where the shape allows.
 // Tensor-core form of launch_multidot for FP32 X and Y (gemm_tc.cu): 3xTF32
 // tcgen05 MMAs, split-K over the SMs, partials summed in FP64. Fields of X
 // (resp. Y) are x_stride (y_stride) bytes apart. scratch: dots_tc_scratch_doubles(a)
 // doubles. err: device word set to 1 if a bounded wait gave up.
 bool dots_tc_supported(int a, const void* X, const void* Y, size_t N);
+// Tensor-core form of the FP32 restart window product (gemm_tc.cu), same
+// contract as launch_window_gemm; supported for m <= 64, 2 nev <= 24, N % 128 == 0.
+bool restart_tc_supported(int m, int two_nev, size_t N);
+cudaError_t launch_restart_tc(SlotState* states, const SlotPtrs* ptrs, int nslots, size_t N, int* err,
+                              cudaStream_t st);
 size_t dots_tc_scratch_doubles(int a);
 cudaError_t prepare_dots_tc();
 cudaError_t launch_dots_tc(int a, const void* X, size_t x_stride, int b, const void* Y, size_t y_stride, size_t N,

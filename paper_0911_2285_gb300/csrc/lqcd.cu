@@ -101,6 +101,7 @@ struct lqcd_ctx {
     double2* dconst = nullptr;      // constants
 
     int dslash_variant = 0;         // operator-kernel shape (autotuned at init); TILED = plane streaming
+    int use_tc = 1;                 // FP32 projections and restart products on the tensor cores
     TileGeom tgeo[MAX_SLOTS + 1] = {};
     bool tile_ok[MAX_SLOTS + 1] = {};
     int* d_err = nullptr;           // device error word of the bounded waits
@@ -516,7 +517,7 @@ lqcd_status deflate_range(lqcd_ctx* c, int s0, int k) {
         R = xl;
         rp = 1;
     }
-    CK(launch_multidot(n, c->Ul, c->kprec, k, R, rp, c->N, C, k, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
+    CK(launch_multidot(n, c->Ul, c->kprec, k, R, rp, c->N, C, k, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err, c->use_tc));
     CK(launch_lu_solve(n, c->Hlu, c->n_def_max, c->Hpiv, 0, k, C, k, c->stream));
     CK(launch_vupdate(n, c->Ur, c->kprec, C, k, k, xh, 0, 0, c->N, c->stream));
     return LQCD_OK;
@@ -557,8 +558,8 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, void* work) {
     CK(launch_norms(nn, Wn, kp, c->N, nrm + nn, c->mdscratch, c->mdscratch_elems, c->stream));
     if (n > 0) {
         // V' = V - U_r M^{-1} U_l^H V ;  W' = W - U_l M^{-H} U_r^H W
-        CK(launch_multidot(n, c->Ul, kp, nn, Vn, kp, c->N, G, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
-        CK(launch_multidot(n, c->Ur, kp, nn, Wn, kp, c->N, G2, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
+        CK(launch_multidot(n, c->Ul, kp, nn, Vn, kp, c->N, G, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err, c->use_tc));
+        CK(launch_multidot(n, c->Ur, kp, nn, Wn, kp, c->N, G2, nn, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err, c->use_tc));
         CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 0, nn, G, nn, c->stream));
         CK(launch_lu_solve(n, c->Mlu, ld, c->Mpiv, 1, nn, G2, nn, c->stream));
         negate_kernel<<<1, 256, 0, c->stream>>>(G, n * nn);
@@ -608,14 +609,14 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, void* work) {
     CK(cudaMemcpyAsync(AW + (size_t)kk * c->kbytes, Wn, (size_t)kk * c->kbytes, cudaMemcpyDeviceToDevice, c->stream));
     // [U_l W']^H [A V' | V'] -> H[:, n:n+kk] and M[:, n:n+kk]  (rows 0..n+kk)
     const int nt = n + kk;
-    CK(launch_multidot(nt, c->Ul, kp, 2 * kk, AV, kp, c->N, T1, 2 * kk, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
+    CK(launch_multidot(nt, c->Ul, kp, 2 * kk, AV, kp, c->N, T1, 2 * kk, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err, c->use_tc));
     copy_block_kernel<<<16, 256, 0, c->stream>>>(T1, 2 * kk, c->Hdef + n, ld, nt, kk);
     copy_block_kernel<<<16, 256, 0, c->stream>>>(T1 + kk, 2 * kk, c->Mdef + n, ld, nt, kk);
     count_launches(2);
     CK(cudaGetLastError());
     if (n > 0) {
         // (A^H W')^H U_r -> H[n:n+kk, 0:n] ;  W'^H U_r -> M[n:n+kk, 0:n]
-        CK(launch_multidot(n, c->Ur, kp, 2 * kk, AW, kp, c->N, T2, n, 1, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
+        CK(launch_multidot(n, c->Ur, kp, 2 * kk, AW, kp, c->N, T2, n, 1, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err, c->use_tc));
         copy_block_kernel<<<16, 256, 0, c->stream>>>(T2, n, c->Hdef + (size_t)n * ld, ld, kk, n);
         copy_block_kernel<<<16, 256, 0, c->stream>>>(T2 + (size_t)kk * n, n, c->Mdef + (size_t)n * ld, ld, kk, n);
         count_launches(2);
@@ -665,7 +666,10 @@ lqcd_status enqueue_chunk(lqcd_ctx* c, int nslots, int windowed) {
         CK(launch_matvec(c, nslots, c->dslash_variant));
         if (windowed) {
             CK(launch_restart_coeffs(c->d_state, c->d_ptrs, nslots, c->eigwork, c->stream));
-            CK(launch_window_gemm(c->kprec, 2 * c->nev, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+            if (c->kprec && c->use_tc && restart_tc_supported(c->m, 2 * c->nev, c->N))
+                CK(launch_restart_tc(c->d_state, c->d_ptrs, nslots, c->N, c->d_err, c->stream));
+            else
+                CK(launch_window_gemm(c->kprec, 2 * c->nev, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
         }
         CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
         CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
@@ -893,9 +897,9 @@ lqcd_status project_fp64(lqcd_ctx* c, int n, double2* Hout, double2* Mout, int l
         lqcd_status s = apply_fields(c, 0, 0, kb, in, c->kprec ? c->dbytes : c->kbytes, c->rt_all, c->dbytes, nullptr);
         if (s != LQCD_OK) return s;
         CK(launch_multidot(n, c->Ul, c->kprec, kb, c->rt_all, 0, c->N, Hout + j0, ld, 0, c->mdscratch,
-                           c->mdscratch_elems, c->stream, c->d_err));
+                           c->mdscratch_elems, c->stream, c->d_err, c->use_tc));
         CK(launch_multidot(n, c->Ul, c->kprec, kb, in, 0, c->N, Mout + j0, ld, 0, c->mdscratch,
-                           c->mdscratch_elems, c->stream, c->d_err));
+                           c->mdscratch_elems, c->stream, c->d_err, c->use_tc));
     }
     return LQCD_OK;
 }
@@ -985,8 +989,8 @@ extern "C" lqcd_status lqcd_eigs(lqcd_ctx* c, int* n_inout, double* evals, doubl
             CK(launch_vupdate(kb, c->x_hi_all, 0, D, kb, kb, c->rt_all, 0, 0, c->N, c->stream));
             double2* gr = D + 256;
             double2* gu = gr + 256;
-            CK(launch_multidot(kb, c->rt_all, 0, kb, c->rt_all, 0, c->N, gr, kb, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
-            CK(launch_multidot(kb, c->x_hi_all, 0, kb, c->x_hi_all, 0, c->N, gu, kb, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err));
+            CK(launch_multidot(kb, c->rt_all, 0, kb, c->rt_all, 0, c->N, gr, kb, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err, c->use_tc));
+            CK(launch_multidot(kb, c->x_hi_all, 0, kb, c->x_hi_all, 0, c->N, gu, kb, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err, c->use_tc));
             std::vector<double2> hr((size_t)kb * kb), hu((size_t)kb * kb);
             CK(cudaMemcpyAsync(hr.data(), gr, sizeof(double2) * kb * kb, cudaMemcpyDeviceToHost, c->stream));
             CK(cudaMemcpyAsync(hu.data(), gu, sizeof(double2) * kb * kb, cudaMemcpyDeviceToHost, c->stream));
@@ -1079,13 +1083,11 @@ extern "C" lqcd_status lqcd_field_dots(int a, const float* X, int b, const float
         e = cudaMemset(derr, 0, 16);
         if (e == cudaSuccess) e = cudaEventCreate(&e0);
         if (e == cudaSuccess) e = cudaEventCreate(&e1);
-        set_dots_path(path);
         for (int r = 0; e == cudaSuccess && r <= reps; ++r) {
             if (r == 1) e = cudaEventRecord(e0, 0);
             if (e == cudaSuccess)
-                e = launch_multidot(a, X, 1, b, Y, 1, N, dC, b, 0, scratch, md_elems, 0, derr);
+                e = launch_multidot(a, X, 1, b, Y, 1, N, dC, b, 0, scratch, md_elems, 0, derr, path);
         }
-        set_dots_path(1);
         if (e == cudaSuccess && reps > 0) e = cudaEventRecord(e1, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e == cudaSuccess && reps > 0) {
@@ -1201,6 +1203,23 @@ extern "C" lqcd_status lqcd_time_kernel(lqcd_ctx* c, int kernel, int k, int reps
 }
 
 extern "C" int lqcd_dslash_variant(const lqcd_ctx* c) { return c ? c->dslash_variant : -1; }
+
+extern "C" lqcd_status lqcd_set_tensor_cores(lqcd_ctx* c, int on) {
+    if (!c) return LQCD_ERR_ARG;
+    if (c->session_busy()) {
+        g_last_error = "lqcd_set_tensor_cores: requests are in flight";
+        return LQCD_ERR_STATE;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->use_tc = on ? 1 : 0;
+    for (int i = 0; i <= MAX_SLOTS; ++i)   // the iteration graphs hold the old kernels
+        for (int j = 0; j < 2; ++j)
+            if (c->graphs[i][j]) {
+                cudaGraphExecDestroy(c->graphs[i][j]);
+                c->graphs[i][j] = nullptr;
+            }
+    return LQCD_OK;
+}
 
 // Autotuner: time every operator-kernel variant on this lattice with a full
 // batch and keep the fastest (FP32 operator only; FP64 has one shape).

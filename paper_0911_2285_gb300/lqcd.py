@@ -103,6 +103,8 @@ def lib():
         L.lqcd_poll.argtypes = [vp, C.c_longlong, C.POINTER(C.c_int), C.POINTER(SolveInfo), C.POINTER(C.c_int)]
         for name in ("lqcd_submit", "lqcd_progress", "lqcd_poll"):
             getattr(L, name).restype = C.c_int
+        L.lqcd_set_tensor_cores.argtypes = [vp, C.c_int]
+        L.lqcd_set_tensor_cores.restype = C.c_int
         L.lqcd_field_dots.argtypes = [C.c_int, vp, C.c_int, vp, C.c_longlong, C.c_int, C.c_int, vp,
                                       C.POINTER(C.c_double)]
         L.lqcd_field_dots.restype = C.c_int
@@ -312,6 +314,10 @@ class Solver:
                                      C.c_void_p(ap.ctypes.data), C.c_void_p(ahp.ctypes.data),
                                      C.c_void_p(sig.ctypes.data)), "lqcd_apply_pair")
         return ap, ahp, sig
+
+    def set_tensor_cores(self, on):
+        """Tensor-core (True, default) or CUDA-core (False) FP32 projections and restart products."""
+        _check(lib().lqcd_set_tensor_cores(self._h, 1 if on else 0), "lqcd_set_tensor_cores")
 
     def dslash_variant(self):
         """Operator-kernel shape chosen by the autotuner."""

@@ -49,6 +49,19 @@ def test_random_fields_fp32_accuracy(path, a, b, n):
     assert np.max(np.abs(c - ref) / bound) <= 2e-6
 
 
+@pytest.mark.parametrize("path", [0, 1])
+def test_norms_without_cancellation(path):
+    """C_ii = |x_i|^2 sums positive terms only: the relative error shows the
+    accumulation itself (the tensor core truncates as it accumulates; short
+    separate runs keep it at FP32 level)."""
+    from paper_0911_2285_gb300.lqcd import field_dots
+    x, X = fields(16, 884736, 77)
+    c, _ = field_dots(X, X, path=path)
+    nrm = np.linalg.norm(x.astype(np.complex128), axis=1) ** 2
+    assert np.max(np.abs(np.diag(c) - nrm) / nrm) <= 1e-6
+    assert np.max(np.abs(np.diag(c).imag)) <= 1e-6 * nrm.max()
+
+
 def test_paths_agree_and_tensor_path_is_faster_at_solver_shape():
     """The growth projection shape of the 24^3x64 solver (80 eigenspace columns
     against 8 fields of 10.6M complex numbers): both paths agree to FP32 level; the
@@ -78,3 +91,39 @@ def test_rejects_unsupported_shape():
     c, _ = lqcd.field_dots(X, Y, path=0)
     bound = np.outer(np.linalg.norm(x, axis=1), np.linalg.norm(y, axis=1))
     assert np.max(np.abs(c - ref_dots(x, y)) / bound) <= 2e-6
+
+
+def test_restart_product_tensor_cores_match_cuda_cores():
+    """eigBiCG with restarts in mixed precision (8^4, m = 40, nev = 10): the window
+    product never feeds back into the BiCG iterates, so both paths give the same x bit
+    for bit and the same iteration and restart counts, and both meet the FP64 true
+    residual with the oracle's A. Stopped just after the first restart, the projected
+    window matrix H (restart Ritz values plus the coupling row and column formed from
+    the new basis vectors) agrees between the paths to FP32 rounding."""
+    from paper_0911_2285_gb300 import Solver
+    from seeded_inputs import z2_source
+    from tests.gpu_util import true_resid, workload
+    w, links, op = workload("8^4")
+    b = z2_source(w["dims"], 4321)
+    full, early = {}, {}
+    with Solver(links, w["dims"], w["kappa"], nev=w["nev"], m=w["m"], n1=1, tol=1e-10, maxiter=4000,
+                precision="mixed", k_max=2) as s:
+        for tc in (True, False):
+            s.set_tensor_cores(tc)
+            s.reset_eigenspace()
+            x, info, _ = s.solve(b, mode="eigbicg")
+            full[tc] = (x[0], info[0], s.last_window()[2])
+    with Solver(links, w["dims"], w["kappa"], nev=w["nev"], m=w["m"], n1=1, tol=1e-10, maxiter=w["m"] + 6,
+                precision="mixed", k_max=2) as s:
+        for tc in (True, False):
+            s.set_tensor_cores(tc)
+            s.solve(b, mode="eigbicg", raise_on_fail=False)   # the second solve starts from a fresh window
+            early[tc] = s.last_window()
+    (x1, i1, n1), (x0, i0, n0) = full[True], full[False]
+    assert i1["iters"] == i0["iters"] and i1["restarts"] == i0["restarts"] and i1["restarts"] >= 3
+    assert n1 == n0
+    assert np.array_equal(x1, x0)
+    assert true_resid(op, b, x1) <= 1e-10
+    (H1, _, r1), (H0, _, r0) = early[True], early[False]
+    assert r1 == r0 == 1 and H1.shape == H0.shape
+    assert np.max(np.abs(H1 - H0)) <= 1e-4 * np.max(np.abs(H0))
