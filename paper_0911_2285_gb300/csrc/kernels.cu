@@ -7,6 +7,7 @@
 // partial sums to a fixed slot, and the last block to finish adds them in
 // block order (same result alone or inside a batch).
 #include "dslash.cuh"
+#include "dfloat.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
 
@@ -532,9 +533,10 @@ __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, c
 // folded into x_hi just before).
 // check_only = 0: inside the iteration (converged if ||r|| <= tol ||b||);
 // check_only = 1: final report for every slot that was started.
-__global__ void __launch_bounds__(DS_THREADS) true_resid_kernel(Geom g, const void* links64, double kappa,
-                                                                SlotState* states, const SlotPtrs* ptrs,
-                                                                int check_only) {
+template <int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) true_resid_kernel(Geom g, const void* links64, double kappa,
+                                                                   SlotState* states, const SlotPtrs* ptrs,
+                                                                   int check_only) {
     SlotState& st = states[blockIdx.y];
     const SlotPtrs& P = ptrs[blockIdx.y];
     if (check_only) {
@@ -565,6 +567,109 @@ __global__ void __launch_bounds__(DS_THREADS) true_resid_kernel(Geom g, const vo
     }
 }
 
+// The in-iteration reliable-update residual b - A x_hi with A x_hi in
+// double-float arithmetic (dfloat.cuh): same contract as true_resid_kernel
+// with check_only = 0.
+// One hop in double-float: each colour row of U h (or U^+ h) is formed and
+// added into the accumulator at once, and the link is read row by row, so
+// only a row of U and one colour of U h are live next to h and the sums.
+template <int MU, int SG>
+__device__ __forceinline__ void recon_row_df(dfc a, dfc b, int c, dfc (&acc)[12]) {
+    dfc l0, l1;   // M^+ (a, b)
+    if (MU == 0) { l0 = mul_i(b); l1 = mul_i(a); }
+    else if (MU == 1) { l0 = b; l1 = -a; }
+    else if (MU == 2) { l0 = mul_i(a); l1 = mul_mi(b); }
+    else { l0 = a; l1 = b; }
+    acc[c] = acc[c] + a;
+    acc[3 + c] = acc[3 + c] + b;
+    if (SG > 0) { acc[6 + c] = acc[6 + c] + l0; acc[9 + c] = acc[9 + c] + l1; }
+    else { acc[6 + c] = acc[6 + c] - l0; acc[9 + c] = acc[9 + c] - l1; }
+}
+template <int MU, bool BWD>
+__device__ __forceinline__ void hop_df(const Nbr& nb, const LinksDF& U, const FieldDF& in, int s, dfc (&acc)[12]) {
+    constexpr int SG = BWD ? +1 : -1;
+    dfc h[2][3];
+    {
+        dfc psi[12];
+        in.load(BWD ? nb.b[MU] : nb.f[MU], psi);
+        project<MU, SG>(psi, h);
+    }
+    const int ls = BWD ? nb.b[MU] : s;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        dfc u[3];   // row r of U (forward) or column r (backward, conjugated below)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 t = __ldg(U.u + (size_t)(MU * 9 + (BWD ? 3 * c + r : 3 * r + c)) * U.V + ls);
+            u[c] = {{t.x, t.z}, {t.y, t.w}};
+        }
+        dfc o[2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            Dot2 re, im;
+            if (!BWD) {
+                re.first(u[0].x, h[a][0].x); re.add(-u[0].y, h[a][0].y);
+                im.first(u[0].x, h[a][0].y); im.add(u[0].y, h[a][0].x);
+#pragma unroll
+                for (int c = 1; c < 3; ++c) {
+                    re.add(u[c].x, h[a][c].x); re.add(-u[c].y, h[a][c].y);
+                    im.add(u[c].x, h[a][c].y); im.add(u[c].y, h[a][c].x);
+                }
+            } else {
+                re.first(u[0].x, h[a][0].x); re.add(u[0].y, h[a][0].y);
+                im.first(u[0].x, h[a][0].y); im.add(-u[0].y, h[a][0].x);
+#pragma unroll
+                for (int c = 1; c < 3; ++c) {
+                    re.add(u[c].x, h[a][c].x); re.add(u[c].y, h[a][c].y);
+                    im.add(u[c].x, h[a][c].y); im.add(-u[c].y, h[a][c].x);
+                }
+            }
+            o[a] = {re.done(), im.done()};
+        }
+        recon_row_df<MU, SG>(o[0], o[1], r, acc);
+    }
+}
+template <int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) true_resid_df_kernel(Geom g, const float4* links_df, double kappa,
+                                                                      SlotState* states, const SlotPtrs* ptrs) {
+    SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (st.status != ST_RUNNING || !st.need_ru) return;
+    const LinksDF U{links_df, g.V};
+    const FieldDF in{P.x_df, g.V};
+    double2 v[1] = {make_double2(0, 0)};
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        const Nbr nb(g, s);
+        dfc acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = {{0.f, 0.f}, {0.f, 0.f}};
+        hop_df<0, false>(nb, U, in, s, acc);
+        hop_df<0, true>(nb, U, in, s, acc);
+        hop_df<1, false>(nb, U, in, s, acc);
+        hop_df<1, true>(nb, U, in, s, acc);
+        hop_df<2, false>(nb, U, in, s, acc);
+        hop_df<2, true>(nb, U, in, s, acc);
+        hop_df<3, false>(nb, U, in, s, acc);
+        hop_df<3, true>(nb, U, in, s, acc);
+        double2 self[12], b[12];
+        Field<double>::load(P.x_hi, g.V, s, self);
+        Field<double>::load(P.b, g.V, s, b);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const double2 a = make_double2(df_value(acc[c].x), df_value(acc[c].y));
+            b[c] = b[c] - (self[c] - kappa * a);
+            v[0].x += cabs2(b[c]);
+        }
+        Field<double>::store(P.r_true, g.V, s, b);
+    }
+    double2 tot[1];
+    if (reduce_slot<1>(P, CNT_RU, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+        st.true_rnorm = sqrt(tot[0].x);
+        st.matvecs += 1;
+        if (st.true_rnorm <= st.tol * st.bnorm) st.status = ST_CONVERGED;
+    }
+}
+
 // Reliable update, first half: x_hi += x_lo, x_lo = 0 for slots that asked for it.
 template <typename S>
 __global__ void __launch_bounds__(BL_THREADS) fold_ru_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
@@ -579,6 +684,11 @@ __global__ void __launch_bounds__(BL_THREADS) fold_ru_kernel(SlotState* states, 
         xh.a = xh.a + to_d(xl.a); xh.b = xh.b + to_d(xl.b);
         xh.store(P.x_hi, u);
         zero.store(P.x_lo, u);
+        if (P.x_df) {   // the double-float copy read by the reliable-update residual
+            const dfl ar = df_split(xh.a.x), ai = df_split(xh.a.y), br = df_split(xh.b.x), bi = df_split(xh.b.y);
+            P.x_df[2 * u] = make_float4(ar.h, ai.h, ar.l, ai.l);
+            P.x_df[2 * u + 1] = make_float4(br.h, bi.h, br.l, bi.l);
+        }
     }
 }
 
@@ -850,6 +960,15 @@ __global__ void __launch_bounds__(WG_T * ((RMAX + WG_K - 1) / WG_K))
 
 }  // namespace
 
+// FP64 links [mu][9][V] double2 -> double-float float4 (h.re, h.im, l.re, l.im).
+__global__ void links_df_kernel(const double2* l64, float4* ldf, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = l64[i];
+        const dfl r = df_split(v.x), m = df_split(v.y);
+        ldf[i] = make_float4(r.h, m.h, r.l, m.l);
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 static Geom geom_of(const Geom& g) { return g; }
 
@@ -961,6 +1080,12 @@ cudaError_t launch_norms(int b, const void* Y, int yp, size_t N, double* out, do
     return cudaGetLastError();
 }
 
+cudaError_t launch_links_df(const double2* l64, float4* ldf, size_t n, cudaStream_t st) {
+    links_df_kernel<<<1216, 256, 0, st>>>(l64, ldf, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scale_fields(int b, void* Y, int yp, const double2* sc, size_t N, cudaStream_t st) {
     int nb = blas_blocks(N * b);
     if (yp == 0) scale_fields_kernel<double><<<nb, BL_THREADS, 0, st>>>(b, Y, sc, N);
@@ -1046,14 +1171,45 @@ cudaError_t launch_bicg_update(int prec, SlotState* states, const SlotPtrs* ptrs
     return cudaGetLastError();
 }
 
+// FP64 true-residual shapes (threads, blocks per SM): FP64 arithmetic runs at a
+// small fraction of the FP32 rate, so occupancy (latency hiding for the FP64
+// pipe) decides; the library times them at init.
+template <int THREADS, int MINB>
+static void true_resid_launch(const Geom& g, const void* links64, double kappa, SlotState* states,
+                              const SlotPtrs* ptrs, int nslots, int check_only, cudaStream_t s) {
+    int nb = div_up((size_t)g.V, THREADS);
+    if (nb > PARTIAL_STRIDE / 2) nb = PARTIAL_STRIDE / 2;
+    true_resid_kernel<THREADS, MINB><<<dim3(nb, nslots), THREADS, 0, s>>>(g, links64, kappa, states, ptrs, check_only);
+}
+int true_resid_variants() { return 6; }
+static void launch_true_resid(int variant, const Geom& g, const void* links64, const float4* links_df,
+                              double kappa, SlotState* states, const SlotPtrs* ptrs, int nslots, int check_only,
+                              cudaStream_t s) {
+    if ((variant == RU_DF || variant == RU_DF + 1) && !check_only && links_df) {
+        int nb = div_up((size_t)g.V, 128);
+        if (nb > PARTIAL_STRIDE / 2) nb = PARTIAL_STRIDE / 2;
+        if (variant == RU_DF)
+            true_resid_df_kernel<128, 4><<<dim3(nb, nslots), 128, 0, s>>>(g, links_df, kappa, states, ptrs);
+        else
+            true_resid_df_kernel<128, 2><<<dim3(nb, nslots), 128, 0, s>>>(g, links_df, kappa, states, ptrs);
+        return;
+    }
+    switch (variant) {
+        case 1: true_resid_launch<128, 3>(g, links64, kappa, states, ptrs, nslots, check_only, s); break;
+        case 2: true_resid_launch<128, 4>(g, links64, kappa, states, ptrs, nslots, check_only, s); break;
+        case 3: true_resid_launch<64, 6>(g, links64, kappa, states, ptrs, nslots, check_only, s); break;
+        default: true_resid_launch<128, 1>(g, links64, kappa, states, ptrs, nslots, check_only, s); break;
+    }
+}
+
 cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int prec, SlotState* states,
-                           const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s) {
+                           const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s, int ru_variant,
+                           const float4* links_df) {
     dim3 g2(blas_blocks(N / 2), nslots);
     if (prec == 0) fold_ru_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     else fold_ru_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     count_launches(1);
-    dim3 grid(ds_blocks(g.V), nslots);
-    true_resid_kernel<<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 0);
+    launch_true_resid(ru_variant, g, links64, links_df, kappa, states, ptrs, nslots, 0, s);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1079,15 +1235,14 @@ cudaError_t launch_bicg_direction(int prec, SlotState* states, const SlotPtrs* p
 }
 
 cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa, int prec, SlotState* states,
-                               const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s) {
+                               const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s, int ru_variant) {
     dim3 g2(blas_blocks(N / 2), nslots);
     if (prec == 0) fold_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     else fold_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 grid(ds_blocks(g.V), nslots);
-    true_resid_kernel<<<grid, DS_THREADS, 0, s>>>(g, links64, kappa, states, ptrs, 1);
+    launch_true_resid(ru_variant >= RU_DF ? 0 : ru_variant, g, links64, nullptr, kappa, states, ptrs, nslots, 1, s);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -89,12 +89,21 @@ bool matvec_variant_ok(const Geom& g, int v);
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec,
                                SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant);
 cudaError_t launch_bicg_update(int prec, SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+// ru_variant: true-residual kernel shape (0 .. true_resid_variants()-1, timed at init);
+// RU_DF and RU_DF + 1 evaluate A x_hi in double-float arithmetic (needs links_df
+// and the slots' x_df); the final residual of launch_bicg_finish is always native FP64.
+constexpr int RU_DF = 4;
+int true_resid_variants();
 cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int prec,
-                           SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+                           SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s,
+                           int ru_variant = 0, const float4* links_df = nullptr);
+// FP64 links -> double-float links (n complex elements).
+cudaError_t launch_links_df(const double2* l64, float4* ldf, size_t n, cudaStream_t st);
 cudaError_t launch_bicg_scalars(SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s);
 cudaError_t launch_bicg_direction(int prec, SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
 cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa, int prec,
-                               SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+                               SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s,
+                               int ru_variant = 0);
 
 // eigBiCG restart: coefficient kernel (one CTA per slot) and window product.
 // Work buffers: eig_work_elems() double2 per slot (restart; the buffer holds MAX_SLOTS

@@ -62,6 +62,8 @@ struct lqcd_ctx {
     std::vector<void*> allocs;
 
     double2* links64 = nullptr;
+    float4* links_df = nullptr;     // double-float links for the reliable-update residual (mixed)
+    float4* xdf_all = nullptr;      // per slot: x_hi as double-float pairs (mixed)
     float4* links32 = nullptr;
 
     SlotState* d_state = nullptr;
@@ -102,6 +104,7 @@ struct lqcd_ctx {
 
     int dslash_variant = 0;         // operator-kernel shape (autotuned at init); TILED = plane streaming
     int use_tc = 1;                 // FP32 projections and restart products on the tensor cores
+    int ru_variant = 0;             // FP64 true-residual kernel shape (timed at init)
     TileGeom tgeo[MAX_SLOTS + 1] = {};
     bool tile_ok[MAX_SLOTS + 1] = {};
     int* d_err = nullptr;           // device error word of the bounded waits
@@ -194,6 +197,7 @@ lqcd_status set_ptrs(lqcd_ctx* c) {
         P.x_hi = c->x_hi_all + (size_t)s * c->N;
         P.b = c->b_all + (size_t)s * c->N;
         P.r_true = c->rt_all + (size_t)s * c->N;
+        P.x_df = c->xdf_all ? c->xdf_all + (size_t)s * c->N : nullptr;
         const size_t wslots = (size_t)(c->m + 1);
         P.V = c->krylov(c->win_all, (size_t)s * 2 * wslots);
         P.W = c->krylov(c->win_all, (size_t)s * 2 * wslots + wslots);
@@ -284,7 +288,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
 
     // Memory plan (bytes) for the HBM budget check.
     const size_t K = (size_t)c->kmax;
-    size_t plan = (size_t)c->V * 4 * 9 * 16 + (c->kprec ? (size_t)c->V * 4 * 3 * 16 : 0);
+    size_t plan = (size_t)c->V * 4 * 9 * 16 + (c->kprec ? (size_t)c->V * 4 * (3 + 9) * 16 + K * c->N * 16 : 0);
     plan += K * c->kbytes * (1 + 2 * (c->m + 1) + 6) + K * c->dbytes * 4;
     plan += 2 * (size_t)c->n_def_max * c->kbytes;
     plan += (MAX_SLOTS * eig_work_elems() + 16) * 16 + c->mdscratch_elems * 16 + K * CNT_COUNT * PARTIAL_STRIDE * 16;
@@ -311,6 +315,8 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     }
     AL(c->links64, (size_t)c->V * 4 * 9 * 16);
     if (c->kprec) AL(c->links32, (size_t)c->V * 4 * 3 * 16);
+    if (c->kprec) AL(c->links_df, (size_t)c->V * 4 * 9 * 16);
+    if (c->kprec) AL(c->xdf_all, K * c->N * 16);
     AL(c->d_state, sizeof(SlotState) * K);
     AL(c->d_ptrs, sizeof(SlotPtrs) * K);
     e = cudaMallocHost(&c->h_state, sizeof(SlotState) * K);
@@ -370,6 +376,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
         count_launches(1);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && c->links_df) e = launch_links_df(c->links64, c->links_df, (size_t)c->V * 4 * 9, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) { set_error("links upload", e); return fail(LQCD_ERR_CUDA); }
@@ -672,7 +679,8 @@ lqcd_status enqueue_chunk(lqcd_ctx* c, int nslots, int windowed) {
                 CK(launch_window_gemm(c->kprec, 2 * c->nev, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
         }
         CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
-        CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+        CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream,
+                          c->ru_variant, c->links_df));
         CK(launch_bicg_scalars(c->d_state, c->d_ptrs, nslots, c->stream));
         CK(launch_bicg_direction(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
     }
@@ -739,7 +747,8 @@ lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol) {
         s = run_chunk(c, k, windowed);
         if (s != LQCD_OK) return s;
     }
-    CK(launch_bicg_finish(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
+    CK(launch_bicg_finish(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream,
+                          c->ru_variant));
     CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SlotState) * k, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LQCD_OK;
@@ -1147,10 +1156,16 @@ constexpr int TIME_TILED = 99;   // lqcd_time_kernel id of the plane-streaming s
 
 static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, double* avg_ms) {
     if (!c || !avg_ms || k < 1 || k > c->kmax || reps < 1) return LQCD_ERR_ARG;
-    if (kernel < 0 || (kernel > 3 && kernel < 10) || (kernel >= 10 + matvec_variants() && kernel != TIME_TILED))
+    if (kernel < 0 || (kernel > 3 && kernel < 10) ||
+        (kernel >= 10 + matvec_variants() && kernel != TIME_TILED && !(kernel >= 40 && kernel < 40 + true_resid_variants())))
         return LQCD_ERR_ARG;
     if (kernel == TIME_TILED && !c->tile_ok[k]) return LQCD_ERR_ARG;
     if (kernel >= 10 && kernel < 10 + matvec_variants() && !matvec_variant_ok(c->g, kernel - 10)) return LQCD_ERR_ARG;
+    const int ru_saved = c->ru_variant;
+    if (kernel >= 40 && kernel < 40 + true_resid_variants()) {   // reliable update with FP64 shape v
+        c->ru_variant = kernel - 40;
+        kernel = 3;
+    }
     // Slots 0..k-1 iterate with fixed scalars on whatever their buffers hold.
     std::vector<SlotState> tmpl(c->kmax);
     for (int s = 0; s < c->kmax; ++s) {
@@ -1181,7 +1196,8 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
                                                      c->stream, kernel - 10));
         else if (kernel == 1) CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
         else if (kernel == 2) CK(launch_bicg_direction(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
-        else CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
+        else CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream,
+                               c->ru_variant, c->links_df));
         CK(cudaEventRecord(e1, c->stream));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -1190,6 +1206,7 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    c->ru_variant = ru_saved;
     // leave the slots idle
     for (int s = 0; s < c->kmax; ++s) { tmpl[s].status = ST_IDLE; tmpl[s].live = 0; }
     CK(cudaMemcpyAsync(c->d_state, tmpl.data(), sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
@@ -1224,6 +1241,18 @@ extern "C" lqcd_status lqcd_set_tensor_cores(lqcd_ctx* c, int on) {
 // Autotuner: time every operator-kernel variant on this lattice with a full
 // batch and keep the fastest (FP32 operator only; FP64 has one shape).
 static lqcd_status autotune(lqcd_ctx* c) {
+    {   // FP64 true-residual shape
+        double best_ru = 1e300;
+        for (int v = 0; v < true_resid_variants(); ++v) {
+            double ms = 0.0;
+            if (v >= RU_DF && !c->links_df) continue;
+            lqcd_status s = time_kernel_impl(c, 40 + v, 1, 1, &ms);
+            if (s != LQCD_OK) return s;
+            s = time_kernel_impl(c, 40 + v, 1, 2, &ms);
+            if (s != LQCD_OK) return s;
+            if (ms < best_ru) { best_ru = ms; c->ru_variant = v; }
+        }
+    }
     if (!c->kprec) return LQCD_OK;
     const int nv = matvec_variants();
     c->tune_ms.assign(nv, 0.0);
@@ -1364,7 +1393,8 @@ lqcd_status admit(lqcd_ctx* c, int s, const lqcd_ctx::Request& req) {
 // the solution back to the caller's buffer.
 lqcd_status retire(lqcd_ctx* c, int s) {
     lqcd_ctx::SlotJob& job = c->jobs[s];
-    CK(launch_bicg_finish(c->g, c->links64, c->p.kappa, c->kprec, c->d_state + s, c->d_ptrs + s, 1, c->N, c->stream));
+    CK(launch_bicg_finish(c->g, c->links64, c->p.kappa, c->kprec, c->d_state + s, c->d_ptrs + s, 1, c->N, c->stream,
+                          c->ru_variant));
     CK(cudaMemcpyAsync(c->h_state + s, c->d_state + s, sizeof(SlotState), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (job.deftol_pending) {

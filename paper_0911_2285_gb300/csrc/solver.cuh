@@ -47,6 +47,7 @@ struct SlotPtrs {
     double2* x_hi;         // FP64 solution
     const double2* b;      // FP64 source
     double2* r_true;       // FP64 scratch for b - A x
+    float4* x_df;          // x_hi as double-float pairs (mixed precision; written by the reliable-update fold)
     void* V;               // residual window: (m+1) fields (windowed) or 1 field
     void* W;               // shadow residual window, same shape
     void* p;
