@@ -319,6 +319,9 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
                                                                int njobs) {
     const int job = blockIdx.x % njobs, sblock = blockIdx.x / njobs, nsb = gridDim.x / njobs;
     const SiteMap<THREADS, BZ> map(g);
+    // each block takes a contiguous run of site units (neighbouring sites stay on one SM)
+    const int per = (map.nunits + nsb - 1) / nsb;
+    const int u0 = sblock * per, u1 = min(map.nunits, u0 + per);
     const int slot = PAIR ? job : job >> 1, which = PAIR ? 0 : job & 1;
     SlotState& st = states[slot];
     const SlotPtrs& P = ptrs[slot];
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
     Acc<S> sacc;   // sigma, |phat|^2, |Ap|^2
     if (PAIR) {
         FieldIn<S> inp{P.p, g.V}, inh{P.phat, g.V};
-        for (int u = sblock; u < map.nunits; u += nsb) {
+        for (int u = u0; u < u1; ++u) {
             const int s = map.site(g, u);
             if (s < 0) continue;
             C a[12], b[12], self[12];
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
     } else {
         FieldIn<S> in{which ? P.phat : P.p, g.V};
         void* out = which ? P.Ahp[par] : P.Ap[par];
-        for (int u = sblock; u < map.nunits; u += nsb) {
+        for (int u = u0; u < u1; ++u) {
             const int s = map.site(g, u);
             if (s < 0) continue;
             C acc[12], self[12];

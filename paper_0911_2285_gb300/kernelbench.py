@@ -8,7 +8,9 @@ the committed ncu captures).
 ``Solver.time_kernel``; after the timed runs each listed shape is launched once
 more (the launches an ncu capture skips to). ``dots``: the inner-product matrix
 X^H Y of FP32 fields on the tensor cores and on the CUDA cores; the last launch
-is one more tensor-core call. Inputs are seeded synthetic fields.
+is one more tensor-core call. ``restart``: eigBiCG on k sources stopped a few
+iterations after the first window restart (the m-th iteration launches the
+tensor-core restart product that does work). Inputs are seeded synthetic fields.
 """
 from __future__ import annotations
 
@@ -23,6 +25,9 @@ def main(argv=None):
     d.add_argument("--k", type=int, default=8)
     d.add_argument("--variants", type=int, nargs="+", default=[2, 4])
     d.add_argument("--reps", type=int, default=5)
+    r = sub.add_parser("restart")
+    r.add_argument("--workload", default="16^3x32")
+    r.add_argument("--k", type=int, default=2)
     t = sub.add_parser("dots")
     t.add_argument("--a", type=int, default=80)
     t.add_argument("--b", type=int, default=8)
@@ -30,6 +35,7 @@ def main(argv=None):
     t.add_argument("--reps", type=int, default=5)
     args = ap.parse_args(argv)
 
+    import numpy as np
     import torch
     from .lqcd import Solver, field_dots
     if args.what == "dhop":
@@ -47,6 +53,15 @@ def main(argv=None):
                 print(f"  shape {v}: {ms:.4f} ms  {alg / ms / 1e6:.0f} GB/s")
             for v in args.variants:
                 s.time_kernel(10 + v, args.k, 1)
+    elif args.what == "restart":
+        from seeded_inputs import WORKLOADS, workload_links, workload_source
+        w = WORKLOADS[args.workload]
+        b = np.stack([workload_source(args.workload, i) for i in range(args.k)])
+        with Solver(workload_links(args.workload), w["dims"], w["kappa"], nev=w["nev"], m=w["m"], n1=args.k,
+                    tol=1e-10, maxiter=w["m"] + 4, precision="mixed", k_max=args.k) as s:
+            _, info, _ = s.solve(b, mode="eigbicg", raise_on_fail=False)
+            print(f"{args.workload}: eigBiCG window m={w['m']} nev={w['nev']}, {args.k} sources, "
+                  f"{info[0]['iters']} iterations, {info[0]['restarts']} restart(s)")
     else:
         g = torch.Generator(device="cuda").manual_seed(5)
         X = torch.randn(args.a, args.n, dtype=torch.complex64, device="cuda", generator=g)
