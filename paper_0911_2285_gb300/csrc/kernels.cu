@@ -33,6 +33,29 @@ int ds_blocks(int V) {
 }
 
 // ------------------------------------------------------------------- apply
+// r = b - A x with FP64 x, b, r and the hop in FP32 arithmetic on FP32 links:
+// the starting and deflation residuals of the mixed-precision solver, which
+// are consumed in FP32 (the reliable updates and the final residual use
+// FP64-class arithmetic). jobs: in = x, aux = b, out = r.
+__global__ void __launch_bounds__(DS_THREADS) residual32_kernel(Geom g, const float4* links, double kappa,
+                                                                const ApplyJob* jobs, int njobs) {
+    const int jid = blockIdx.x % njobs, sblock = blockIdx.x / njobs, nsb = gridDim.x / njobs;
+    const ApplyJob jb = jobs[jid];
+    LinksF U{links, g.V};
+    FieldIn<double> in{jb.in, g.V};
+    const double k = kappa;
+    for (int s = sblock * blockDim.x + threadIdx.x; s < g.V; s += nsb * blockDim.x) {
+        float2 acc[12];
+        hop_site<false, float>(g, U, in, s, acc);
+        double2 x[12], b[12];
+        Field<double>::load(jb.in, g.V, s, x);
+        Field<double>::load(jb.aux, g.V, s, b);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) b[c] = b[c] - (x[c] - k * to_d(acc[c]));
+        Field<double>::store(jb.out, g.V, s, b);
+    }
+}
+
 template <typename S, bool RES>
 __global__ void __launch_bounds__(DS_THREADS) apply_kernel(Geom g, const void* links, double kappa,
                                                            const ApplyJob* jobs, int njobs) {
@@ -990,6 +1013,14 @@ cudaError_t launch_apply(const Geom& g, const void* links, double kappa, int pre
         if (residual) return cudaErrorInvalidValue;
         apply_kernel<float, false><<<grid, DS_THREADS, 0, st>>>(geom_of(g), links, kappa, d_jobs, njobs);
     }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual32(const Geom& g, const void* links32, double kappa, const ApplyJob* d_jobs, int njobs,
+                              cudaStream_t st) {
+    const int grid = ds_blocks(g.V) * njobs;
+    residual32_kernel<<<grid, DS_THREADS, 0, st>>>(g, reinterpret_cast<const float4*>(links32), kappa, d_jobs, njobs);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -29,6 +29,10 @@ struct ApplyJob {            // out = A in, A^+ in, or aux - A in
 cudaError_t launch_apply(const Geom& g, const void* links, double kappa, int precision,
                          const ApplyJob* d_jobs, int njobs, int residual, cudaStream_t st);
 
+// r = b - A x (FP64 fields) with the hop in FP32 on FP32 links; jobs: in = x, aux = b, out = r.
+cudaError_t launch_residual32(const Geom& g, const void* links32, double kappa, const ApplyJob* d_jobs, int njobs,
+                              cudaStream_t st);
+
 // Host AoS complex128 [site][12] <-> device layout in storage precision.
 cudaError_t launch_pack(const double* aos, void* dev, int V, int k, int precision, cudaStream_t st);
 cudaError_t launch_unpack(const void* dev, double* aos, int V, int k, int precision, cudaStream_t st);

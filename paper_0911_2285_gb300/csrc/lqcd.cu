@@ -480,6 +480,26 @@ lqcd_status apply_fields(lqcd_ctx* c, int prec, int dagger, int nf, const void* 
     return LQCD_OK;
 }
 
+// r = b - A x for nf FP64 fields (consecutive slots): FP32 hop arithmetic in
+// mixed precision (the result feeds FP32 work), FP64 otherwise.
+lqcd_status residual_fields(lqcd_ctx* c, int nf, const double2* x, double2* r, const double2* b) {
+    if (!c->kprec) return apply_fields(c, 0, 0, nf, x, c->dbytes, r, c->dbytes, b);
+    std::vector<ApplyJob> jobs(2 * c->kmax);
+    for (int j0 = 0; j0 < nf; j0 += 2 * c->kmax) {
+        const int nb = std::min(2 * c->kmax, nf - j0);
+        for (int j = 0; j < nb; ++j) {
+            jobs[j].in = x + (size_t)(j0 + j) * c->N;
+            jobs[j].out = r + (size_t)(j0 + j) * c->N;
+            jobs[j].aux = b + (size_t)(j0 + j) * c->N;
+            jobs[j].dagger = 0;
+        }
+        CK(cudaMemcpyAsync(c->d_jobs, jobs.data(), sizeof(ApplyJob) * nb, cudaMemcpyHostToDevice, c->stream));
+        CK(launch_residual32(c->g, c->links32, c->p.kappa, c->d_jobs, nb, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return LQCD_OK;
+}
+
 }  // namespace
 
 extern "C" lqcd_status lqcd_apply(lqcd_ctx* c, int dagger, lqcd_precision prec, int k, const double* in, double* out,
@@ -513,7 +533,7 @@ lqcd_status deflate_range(lqcd_ctx* c, int s0, int k) {
     if (n == 0 || k == 0) return LQCD_OK;
     double2* xh = c->x_hi_all + (size_t)s0 * c->N;
     double2* rt = c->rt_all + (size_t)s0 * c->N;
-    lqcd_status s = apply_fields(c, 0, 0, k, xh, c->dbytes, rt, c->dbytes, c->b_all + (size_t)s0 * c->N);
+    lqcd_status s = residual_fields(c, k, xh, rt, c->b_all + (size_t)s0 * c->N);
     if (s != LQCD_OK) return s;
     double2* C = c->dsmall;   // n x k, ld k
     const void* R = rt;
@@ -725,7 +745,7 @@ lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol) {
     }
     CK(cudaMemcpyAsync(c->d_state, c->h_state, sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
     // r0 = b - A x0 (FP64), then the Krylov start vectors
-    lqcd_status s = apply_fields(c, 0, 0, k, c->x_hi_all, c->dbytes, c->rt_all, c->dbytes, c->b_all);
+    lqcd_status s = residual_fields(c, k, c->x_hi_all, c->rt_all, c->b_all);
     if (s != LQCD_OK) return s;
     CK(launch_bicg_start(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
     while (true) {
@@ -1356,8 +1376,8 @@ lqcd_status begin_slot(lqcd_ctx* c, int s, lqcd_mode md, double tol) {
     st.m = md == LQCD_MODE_EIGBICG ? c->m : 0;
     st.nev = c->nev;
     CK(cudaMemcpyAsync(c->d_state + s, &st, sizeof(SlotState), cudaMemcpyHostToDevice, c->stream));
-    lqcd_status r = apply_fields(c, 0, 0, 1, c->x_hi_all + (size_t)s * c->N, c->dbytes,
-                                 c->rt_all + (size_t)s * c->N, c->dbytes, c->b_all + (size_t)s * c->N);
+    lqcd_status r = residual_fields(c, 1, c->x_hi_all + (size_t)s * c->N, c->rt_all + (size_t)s * c->N,
+                                    c->b_all + (size_t)s * c->N);
     if (r != LQCD_OK) return r;
     CK(launch_bicg_start(c->g, c->links64, c->p.kappa, c->kprec, c->d_state + s, c->d_ptrs + s, 1, c->N, c->stream));
     return LQCD_OK;
