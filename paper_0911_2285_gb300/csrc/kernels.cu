@@ -502,8 +502,10 @@ __global__ void __launch_bounds__(32 * JPB, MINB)
     }
 }
 
-// x_lo += alpha p; r_j = r_{j-1} - alpha A p; rhat_j = rhat_{j-1} - conj(alpha) A^+ phat;
-// rho_j, ||r_j||, ||rhat_j||; flags for the FP64 residual check.
+// r_j = r_{j-1} - alpha A p; rhat_j = rhat_{j-1} - conj(alpha) A^+ phat;
+// rho_j, ||r_j||, ||rhat_j||; flags for the FP64 residual check. The solution
+// update x_lo += alpha p is owed (x_owed): the direction update, which reads p
+// anyway, or the reliable-update fold, or the final fold adds it.
 template <typename S>
 __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
     SlotState& st = states[blockIdx.y];
@@ -521,13 +523,10 @@ __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, c
     Acc<S> acc;   // rho_j, |r_j|^2, |rhat_j|^2
     const size_t units = N / 2;
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
-        Unit<S> x = Unit<S>::load(P.x_lo, u), p = Unit<S>::load(P.p, u);
         Unit<S> r = Unit<S>::load(rin, u), a = Unit<S>::load(ap, u);
         Unit<S> h = Unit<S>::load(hin, u), ah = Unit<S>::load(ahp, u);
-        x.a = x.a + al * p.a; x.b = x.b + al * p.b;
         r.a = r.a - al * a.a; r.b = r.b - al * a.b;
         h.a = h.a - alc * ah.a; h.b = h.b - alc * ah.b;
-        x.store(P.x_lo, u);
         r.store(rout, u);
         h.store(hout, u);
         acc.z = acc.z + cdot(h.a, r.a) + cdot(h.b, r.b);
@@ -541,6 +540,7 @@ __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, c
         st.rho_new = tot[0];
         st.rnorm_new = sqrt(tot[1].x);
         st.rhat_norm = sqrt(tot[1].y);
+        st.x_owed = 1;
         if (!isfinite(st.rnorm_new) || !isfinite(st.rho_new.x) || !isfinite(st.rho_new.y)) {
             st.status = ST_BREAKDOWN;
         } else {
@@ -703,10 +703,15 @@ __global__ void __launch_bounds__(BL_THREADS) fold_ru_kernel(SlotState* states, 
     const SlotPtrs& P = ptrs[blockIdx.y];
     if (st.status != ST_RUNNING || !st.need_ru) return;
     const size_t units = N / 2;
+    const cplx<S> al = cvt<S>(st.alpha);
     Unit<S> zero{mk<S>(0, 0), mk<S>(0, 0)};
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
         Unit<double> xh = Unit<double>::load(P.x_hi, u);
         Unit<S> xl = Unit<S>::load(P.x_lo, u);
+        if (st.x_owed) {   // alpha p of this iteration's residual update
+            const Unit<S> p = Unit<S>::load(P.p, u);
+            xl.a = xl.a + al * p.a; xl.b = xl.b + al * p.b;
+        }
         xh.a = xh.a + to_d(xl.a); xh.b = xh.b + to_d(xl.b);
         xh.store(P.x_hi, u);
         zero.store(P.x_lo, u);
@@ -750,6 +755,7 @@ __global__ void __launch_bounds__(BL_THREADS) replace_kernel(SlotState* states, 
         }
         st.need_ru = 0;
         st.ru_count += 1;
+        st.x_owed = 0;   // the fold added alpha p
     }
 }
 
@@ -789,6 +795,10 @@ __global__ void scalars_kernel(SlotState* states, const SlotPtrs* ptrs) {
         else if (!(cabs_(st.rho) >= BREAK_TOL * st.rhat_norm * st.rnorm)) st.status = ST_BREAKDOWN;
     }
     if (st.status != ST_RUNNING) st.live = 0;
+    // the direction update adds the owed alpha p; a slot that stops here keeps it
+    // owed for the final fold
+    if (st.status == ST_RUNNING) { st.x_dir = st.x_owed; st.x_owed = 0; }
+    else st.x_dir = 0;
 }
 
 // p_j = r_j + beta p_{j-1}, phat_j = rhat_j + conj(beta) phat_{j-1}.
@@ -799,12 +809,19 @@ __global__ void __launch_bounds__(BL_THREADS) direction_kernel(SlotState* states
     if (st.status != ST_RUNNING) return;
     using C = cplx<S>;
     const C be = cvt<S>(st.beta), bec = conj_(be);
+    const C al = cvt<S>(st.alpha);
+    const bool addx = st.x_dir != 0;
     const void* r = slot_field<S>(P.V, cur_slot(st), N);
     const void* h = slot_field<S>(P.W, cur_slot(st), N);
     const size_t units = N / 2;
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
         Unit<S> p = Unit<S>::load(P.p, u), ph = Unit<S>::load(P.phat, u);
         Unit<S> rr = Unit<S>::load(r, u), hh = Unit<S>::load(h, u);
+        if (addx) {   // x_lo += alpha p_{j-1} (owed by the residual update)
+            Unit<S> x = Unit<S>::load(P.x_lo, u);
+            x.a = x.a + al * p.a; x.b = x.b + al * p.b;
+            x.store(P.x_lo, u);
+        }
         p.a = rr.a + be * p.a; p.b = rr.b + be * p.b;
         ph.a = hh.a + bec * ph.a; ph.b = hh.b + bec * ph.b;
         p.store(P.p, u);
@@ -819,11 +836,17 @@ __global__ void fold_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
     const SlotPtrs& P = ptrs[blockIdx.y];
     if (st.status == ST_IDLE) return;
     const bool zero_src = st.bnorm == 0.0;
+    const bool owed = st.x_owed != 0;   // the last residual update's alpha p (no direction update ran)
+    const cplx<S> al = cvt<S>(st.alpha);
     const size_t units = N / 2;
     Unit<S> zero{mk<S>(0, 0), mk<S>(0, 0)};
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
         Unit<double> xh = Unit<double>::load(P.x_hi, u);
         Unit<S> xl = Unit<S>::load(P.x_lo, u);
+        if (owed) {
+            const Unit<S> p = Unit<S>::load(P.p, u);
+            xl.a = xl.a + al * p.a; xl.b = xl.b + al * p.b;
+        }
         if (zero_src) { xh.a = make_double2(0, 0); xh.b = make_double2(0, 0); }
         else { xh.a = xh.a + to_d(xl.a); xh.b = xh.b + to_d(xl.b); }
         xh.store(P.x_hi, u);

@@ -37,6 +37,8 @@ struct SlotState {
     int restart_r;        // vectors kept by the restart in this iteration (0 = none)
     int matvecs;
     int live;             // 1 while the slot takes part in the current iteration
+    int x_owed;           // 1: x_lo has not yet received alpha p of the last residual update
+    int x_dir;            // 1: the direction update adds alpha p to x_lo in this iteration
     int pad;
 };
 
