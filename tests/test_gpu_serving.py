@@ -129,3 +129,26 @@ def test_serving_loop_two_operators():
     for r in reqs:
         assert r.status == 0
         assert true_resid(ops[r.op], r.b, r.x) <= 1e-10
+
+
+def test_session_edge_cases():
+    """A zero source completes with x = 0; a request that hits maxiter reports
+    LQCD_ERR_NOCONV without disturbing the request beside it; unknown tickets and
+    switching the tensor-core path while requests are in flight are refused."""
+    from paper_0911_2285_gb300 import lqcd
+    s, op, w = solver("4^4", k_max=2, maxiter=6)
+    b = workload_source("4^4", 0)
+    z = np.zeros_like(b)
+    xz, xb = np.zeros_like(b), np.zeros_like(b)
+    with s:
+        tz = s.submit(z, xz, mode="plain")
+        tb = s.submit(b, xb, mode="plain")
+        with pytest.raises(lqcd.LQCDError) as e:
+            s.set_tensor_cores(False)
+        assert e.value.status == lqcd.ERR_STATE
+        res = drain(s, [tz, tb])
+        with pytest.raises(lqcd.LQCDError):
+            s.poll(10 ** 9)
+        s.set_tensor_cores(True)   # free again
+    assert res[tz][1] == lqcd.OK and np.all(xz == 0)
+    assert res[tb][1] == lqcd.ERR_NOCONV and res[tb][0]["iters"] == 6
