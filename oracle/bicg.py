@@ -154,13 +154,14 @@ def restart_coefficients(H, nev):
     return yt @ u, zt @ q, lam
 
 
-def eigbicg(op, b, nev, m, x0=None, tol=1e-10, maxiter=10000, snapshot_every=0):
+def eigbicg(op, b, nev, m, x0=None, tol=1e-10, maxiter=10000, snapshot_every=0, rhat0=None):
     """Algorithm eigBiCG(nev, m): BiCG plus a window of m residuals.
 
     Returns a :class:`SolveResult` carrying x, the final nev Ritz values and
     right/left Ritz vectors, and the final window (for identity checks).
     ``snapshot_every > 0`` stores ``(V, W, H)`` copies of the active window at
-    the end of every ``snapshot_every``-th iteration.
+    the end of every ``snapshot_every``-th iteration. ``rhat0`` replaces the
+    shadow start ``r_0`` (Sec. 4: ``gamma5 r_0`` for gamma5-Hermitian A).
     """
     if m <= 2 * nev:
         raise ValueError("eigBiCG needs m > 2 nev")
@@ -170,7 +171,7 @@ def eigbicg(op, b, nev, m, x0=None, tol=1e-10, maxiter=10000, snapshot_every=0):
     mv0 = op.matvecs
     # Steps 1-2: initial residuals, directions, rho_0, vs = 0.
     r = b - op.apply(x)
-    rhat = r.copy()
+    rhat = r.copy() if rhat0 is None else np.array(rhat0, dtype=np.complex128)
     p = r.copy()
     phat = rhat.copy()
     rho = _dot(rhat, r)
@@ -283,3 +284,58 @@ def eigbicg(op, b, nev, m, x0=None, tol=1e-10, maxiter=10000, snapshot_every=0):
         res.U = np.zeros((n, 0), dtype=np.complex128)
         res.Q = np.zeros((n, 0), dtype=np.complex128)
     return res
+
+
+def bicg_g5(op, b, x0=None, tol=1e-10, maxiter=10000, history=False):
+    """BiCG for gamma5-Hermitian A (Sec. 4): with the shadow start
+    ``rhat_0 = gamma5 r_0`` the shadow sequences are ``rhat_j = gamma5 r_j`` and
+    ``phat_j = gamma5 p_j``, so ``A^H phat = gamma5 (A p)``: one product with A
+    per iteration, no shadow vectors. ``rho = r^H gamma5 r`` and
+    ``sigma = p^H gamma5 A p`` are real (gamma5 A is Hermitian), hence real
+    alpha and beta. ``op`` supplies ``apply`` and ``gamma5``.
+    """
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128)
+    mv0 = op.matvecs
+    r = b - op.apply(x)
+    p = r.copy()
+    rho = float(np.real(_dot(op.gamma5(r), r)))
+    bnorm = np.linalg.norm(b)
+    rnorm = np.linalg.norm(r)
+    hist = [rnorm]
+    scal = []
+    if rnorm <= tol * bnorm:
+        return SolveResult(x, 0, op.matvecs - mv0, rnorm / bnorm, hist)
+    j = 0
+    while j < maxiter:
+        j += 1
+        if abs(rho) < BREAKDOWN_TOL * rnorm * rnorm:
+            raise Breakdown(f"rho breakdown at iteration {j}")
+        ap = op.apply(p)
+        g5ap = op.gamma5(ap)            # = A^H phat with phat = gamma5 p
+        sigma = float(np.real(_dot(p, g5ap)))
+        if abs(sigma) < BREAKDOWN_TOL * np.linalg.norm(p) * np.linalg.norm(ap):
+            raise Breakdown(f"sigma breakdown at iteration {j}")
+        alpha = rho / sigma
+        x = x + alpha * p
+        r = r - alpha * ap
+        rho_new = float(np.real(_dot(op.gamma5(r), r)))
+        beta = rho_new / rho
+        p = r + beta * p
+        rho = rho_new
+        rnorm = np.linalg.norm(r)
+        hist.append(rnorm)
+        if history:
+            scal.append((alpha, beta))
+        if rnorm <= tol * bnorm:
+            true_r = b - op.apply(x)
+            tn = np.linalg.norm(true_r)
+            if tn <= tol * bnorm:
+                res = SolveResult(x, j, op.matvecs - mv0, tn / bnorm, hist)
+                if history:
+                    res.snapshots = scal
+                return res
+            r = true_r
+            rho = float(np.real(_dot(op.gamma5(r), r)))
+            rnorm = tn
+    raise NoConvergence(f"gamma5 BiCG: no convergence in {maxiter} iterations")
