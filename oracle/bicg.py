@@ -339,3 +339,61 @@ def bicg_g5(op, b, x0=None, tol=1e-10, maxiter=10000, history=False):
             rho = float(np.real(_dot(op.gamma5(r), r)))
             rnorm = tn
     raise NoConvergence(f"gamma5 BiCG: no convergence in {maxiter} iterations")
+
+
+def bicgstab(op, b, x0=None, tol=1e-10, maxiter=10000, callback=None):
+    """BiCGStab (van der Vorst 1992), the paper's phase-2 solver (Sec. 2), with
+    the shadow start ``rhat = r_0``: each step is a BiCG step followed by a
+    one-dimensional minimal-residual step, two products with A and none with
+    A^H. Convergence on the recursive residual is confirmed with the true one
+    (replaced and continued if it fails, as for BiCG above).
+    ``callback(j, x, r, t)`` sees every iterate and ``t = A s`` of the step
+    (the minimal-residual step makes the new ``r`` orthogonal to ``t``).
+    """
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128)
+    mv0 = op.matvecs
+    r = b - op.apply(x)
+    rhat = r.copy()
+    bnorm = np.linalg.norm(b)
+    rnorm = np.linalg.norm(r)
+    hist = [rnorm]
+    if rnorm <= tol * bnorm:
+        return SolveResult(x, 0, op.matvecs - mv0, rnorm / bnorm, hist)
+    rho_old = alpha = omega = 1.0 + 0j
+    p = np.zeros_like(b)
+    v = np.zeros_like(b)
+    j = 0
+    while j < maxiter:
+        j += 1
+        rho = _dot(rhat, r)
+        if abs(rho) < BREAKDOWN_TOL * np.linalg.norm(rhat) * rnorm:
+            raise Breakdown(f"rho breakdown at iteration {j}")
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = op.apply(p)
+        den = _dot(rhat, v)
+        if abs(den) < BREAKDOWN_TOL * np.linalg.norm(rhat) * np.linalg.norm(v):
+            raise Breakdown(f"(rhat, A p) breakdown at iteration {j}")
+        alpha = rho / den
+        s = r - alpha * v
+        t = op.apply(s)
+        tt = _dot(t, t).real
+        omega = _dot(t, s) / tt if tt > 0 else 0.0 + 0j
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        rho_old = rho
+        rnorm = np.linalg.norm(r)
+        hist.append(rnorm)
+        if callback is not None:
+            callback(j, x, r, t)
+        if rnorm <= tol * bnorm:
+            true_r = b - op.apply(x)
+            tn = np.linalg.norm(true_r)
+            if tn <= tol * bnorm:
+                return SolveResult(x, j, op.matvecs - mv0, tn / bnorm, hist)
+            r = true_r
+            rnorm = tn
+        if omega == 0:
+            raise Breakdown(f"omega breakdown at iteration {j}")
+    raise NoConvergence(f"BiCGStab: no convergence in {maxiter} iterations")

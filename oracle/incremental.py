@@ -34,7 +34,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.linalg as sla
 
-from .bicg import bicg, eigbicg
+from .bicg import bicg, bicgstab, eigbicg
 from .smalleig import order_smallest
 
 DROP_TOL = 1e-8
@@ -131,6 +131,26 @@ def deflated_bicg(op, space, b, x0=None, tol=1e-10, deftol=0.0, maxiter=10000):
         x = deflate(op, space, b, res.x)
     res = bicg(op, b, x, tol=tol, maxiter=maxiter - iters)
     return res.x, iters + res.iters, mv + res.matvecs, res.true_resid
+
+
+def deflated_bicgstab(op, space, b, x0=None, tol=1e-10, deftol=0.0, maxiter=10000):
+    """Phase 2 as the paper runs it (Sec. 2): deflate the initial guess, solve
+    with BiCGStab; with ``deftol > tol`` stop at ``deftol``, deflate the current
+    iterate again and continue to ``tol`` (one restart)."""
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128)
+    x = deflate(op, space, b, x)
+    outer = 0
+    iters = 0
+    if deftol > tol and space.size > 0:
+        first = bicgstab(op, b, x, tol=deftol, maxiter=maxiter)
+        iters += first.iters
+        x = deflate(op, space, b, first.x)
+        outer = 1
+    res = bicgstab(op, b, x, tol=tol, maxiter=maxiter)
+    res.iters += iters
+    res.restarts = outer
+    return res
 
 
 def incremental_eigbicg(op, sources, nev, m, n1, tol=1e-10, deftol=0.0, maxiter=10000,
