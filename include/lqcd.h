@@ -63,7 +63,9 @@ typedef enum {
 typedef enum {
     LQCD_FP64 = 0,   /* every vector and all arithmetic in FP64 */
     LQCD_MIXED = 1   /* FP32 Krylov vectors/links (third-row reconstruction),
-                        FP64 solution, true residual and small dense algebra */
+                        FP64 solution and small dense algebra; reliable updates
+                        against a double-float (or FP64) true residual; the
+                        reported residual of each solution is native FP64 */
 } lqcd_precision;
 
 typedef enum {
@@ -94,7 +96,7 @@ typedef struct {
     int iters;               /* BiCG iterations */
     int matvecs;             /* products with A or A^+ (the paper's cost unit, Sec. 3) */
     int restarts;            /* BiCG-eigen restarts (eigBiCG mode) */
-    int reliable_updates;    /* FP64 true-residual recomputations */
+    int reliable_updates;    /* true-residual recomputations inside the iteration */
     int outer_steps;         /* DefTol re-deflation restarts */
     double true_resid;       /* ||b - A x|| / ||b|| in FP64 at return */
     double seconds;          /* wall time of this right-hand side's batch */
