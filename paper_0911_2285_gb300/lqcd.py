@@ -13,6 +13,7 @@ there is no fallback: a missing library raises ``RuntimeError``.
 from __future__ import annotations
 
 import ctypes as C
+import hashlib
 import os
 
 import numpy as np
@@ -155,6 +156,14 @@ def _ptr(a, n_expected=None):
     return C.c_void_p(a.ctypes.data), 0
 
 
+def _fingerprint(a):
+    """Short digest of a gauge field (shape and a strided sample), to refuse an
+    eigenspace saved for another field."""
+    flat = a.reshape(-1)
+    sample = np.ascontiguousarray(flat[:: max(1, flat.size // 65536)])
+    return hashlib.sha256(repr(a.shape).encode() + sample.tobytes()).hexdigest()[:32]
+
+
 class Solver:
     """One gauge field + parameter set (an ``lqcd_ctx``)."""
 
@@ -163,6 +172,8 @@ class Solver:
                  delta=0.0, stream=None):
         links = np.ascontiguousarray(links, dtype=np.complex128)
         self.dims = tuple(int(d) for d in dims)
+        self.kappa = float(kappa)
+        self._links_fp = _fingerprint(links)
         self.volume = int(np.prod(self.dims))
         self.n = 12 * self.volume
         if links.size != 4 * self.volume * 9:
@@ -343,6 +354,26 @@ class Solver:
             raise ValueError("Ur and Ul must have the same shape")
         _check(lib().lqcd_eigspace_set(self._h, ur.shape[0], C.c_void_p(ur.ctypes.data),
                                        C.c_void_p(ul.ctypes.data)), "lqcd_eigspace_set")
+
+    def save_eigenspace(self, path):
+        """Checkpoint the accumulated eigenspace (U_r, U_l and H = U_l^H A U_r) with
+        the lattice, kappa and a digest of the gauge field, as an ``.npz`` file."""
+        ur, ul, h = self.eigspace_get()
+        np.savez(path, Ur=ur, Ul=ul, H=h, dims=np.array(self.dims), kappa=np.float64(self.kappa),
+                 links_fp=np.array(self._links_fp))
+
+    def load_eigenspace(self, path):
+        """Resume from :meth:`save_eigenspace`: the vectors are installed and H is
+        recomputed on this context's operator (which must be the same gauge field,
+        lattice and kappa, else ``ValueError``). The loaded vectors count as complete
+        eigBiCG solves for AUTO mode."""
+        with np.load(path) as d:
+            if tuple(int(x) for x in d["dims"]) != self.dims or float(d["kappa"]) != self.kappa:
+                raise ValueError("eigenspace saved for another lattice or kappa")
+            if str(d["links_fp"]) != self._links_fp:
+                raise ValueError("eigenspace saved for another gauge field")
+            ur, ul = d["Ur"], d["Ul"]
+        self.eigspace_set(ur, ul)
 
     def last_window(self, slot=0):
         m = self.params.m

@@ -243,3 +243,31 @@ def test_second_eigbicg_solve_starts_a_fresh_window():
         h2, l2, r2 = s.last_window()
     assert r1 == r2 and r1 >= 3
     assert np.array_equal(h1, h2) and np.array_equal(l1, l2)
+
+
+def test_eigenspace_checkpoint_resume(tmp_path):
+    """Checkpoint/resume of the accumulated eigenspace: a new context on the same
+    gauge field loads the saved U_r, U_l (H recomputed on its operator) and deflates
+    like the original; a context with another kappa refuses the file."""
+    from paper_0911_2285_gb300 import Solver
+    s, op, w = solver("4^4", precision="mixed", n1=1, k_max=2)
+    b1, b2 = z2_source(w["dims"], 8800), z2_source(w["dims"], 8801)
+    path = tmp_path / "space.npz"
+    with s:
+        s.solve(b1, mode="eigbicg")
+        ur, ul, H = s.eigspace_get()
+        s.save_eigenspace(path)
+        _, i1, _ = s.solve(b2, mode="deflated")
+    s2, _, _ = solver("4^4", precision="mixed", n1=1, k_max=2)
+    with s2:
+        s2.load_eigenspace(path)
+        ur2, ul2, H2 = s2.eigspace_get()
+        x2, i2, _ = s2.solve(b2, mode="deflated")
+    assert ur.shape[0] > 0 and np.array_equal(ur, ur2) and np.array_equal(ul, ul2)
+    assert np.abs(H2 - H).max() <= 1e-5 * np.abs(H).max()
+    assert abs(i1[0]["iters"] - i2[0]["iters"]) <= 2
+    assert true_resid(op, b2, x2[0]) <= 1e-10
+    _, links, _ = workload("4^4")
+    with Solver(links, w["dims"], 0.11, nev=w["nev"], m=w["m"], precision="mixed", k_max=1) as s3:
+        with pytest.raises(ValueError):
+            s3.load_eigenspace(path)
