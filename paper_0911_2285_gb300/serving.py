@@ -21,6 +21,8 @@ import numpy as np
 
 from .lqcd import Solver
 
+POLL_S = 20e-6   # host pause between non-blocking polls when nothing finished
+
 
 @dataclass
 class Request:
@@ -107,12 +109,14 @@ class Server:
             # one only when nothing else can happen meanwhile
             busy = [n for n in self.ops if pending[n] or active[n]]
             wait = len(busy) == 1 and (not realtime or i == len(reqs))
+            finished = 0
             for name in busy:
                 solver = self.ops[name]
                 active[name] = solver.progress(wait=wait)
                 for ticket in list(pending[name]):
                     done, info, status = solver.poll(ticket)
                     if done:
+                        finished += 1
                         r = pending[name].pop(ticket)
                         r.t_done = time.perf_counter() - t0
                         r.info, r.status = info, status
@@ -125,5 +129,7 @@ class Server:
                 wait_s = reqs[i].t_arrival - (time.perf_counter() - t0)
                 if wait_s > 0:
                     time.sleep(wait_s)
+            elif not wait and busy and not finished:
+                time.sleep(POLL_S)   # nothing finished: yield the core briefly instead of spinning
         rep.makespan = time.perf_counter() - t0
         return rep, reqs
