@@ -275,13 +275,30 @@ lqcd_status lqcd_field_dots(int a, const float *X, int b, const float *Y, long l
  * GPU that loads the library until the process exits).  n > 80 returns
  * LQCD_ERR_ARG.  The first call on a device looks up that array's device
  * address and sets the kernel's shared-memory limit, so make the first call
- * before any stream capture.  Work is ordered on 'cuda_stream' (cudaStream_t,
- * NULL = default stream) and the call returns after it completes.  All calls on
+ * before any stream capture; that set-up is kept for the life of the process
+ * (a cudaDeviceReset between calls is not supported).  Work is ordered on
+ * 'cuda_stream' (cudaStream_t, NULL = default stream) and the call returns
+ * after it completes.  All calls on
  * a device share the scratch array and it keeps the last call's contents: calls
  * whose kernels overlap on the GPU (other streams, other host threads) race.
  * LQCD_ERR_NOCONV if the QR iteration did not converge. */
 lqcd_status lqcd_small_eig_noalloc(int n, const double *C, double *evals, double *Y, double *Z,
                                    void *cuda_stream);
+
+/* Failure-detection hook (no counterpart in the paper): bound of every
+ * device-side wait in this library's kernels (TMA/mbarrier pipelines, the flag
+ * wait below), in SM clock cycles, on the current device.  A kernel whose wait
+ * runs out records an error word and returns; the call that launched it then
+ * returns LQCD_ERR_TIMEOUT.  cycles <= 0 restores the default (4e9 cycles,
+ * about 2 s at 2 GHz).  Affects kernels launched after the call. */
+lqcd_status lqcd_set_wait_limit(long long cycles);
+
+/* Failure-detection hook: one kernel whose single thread waits, with the
+ * library's bounded wait, for the device word *flag (DEVICE pointer) to become
+ * nonzero.  LQCD_OK if it was (or became) nonzero within the limit,
+ * LQCD_ERR_TIMEOUT if the wait gave up.  Ordered on 'cuda_stream' (NULL =
+ * default stream); returns after the kernel has finished. */
+lqcd_status lqcd_wait_flag(const int *flag, void *cuda_stream);
 
 /* Text for a status code. */
 const char *lqcd_status_str(lqcd_status s);

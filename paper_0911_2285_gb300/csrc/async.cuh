@@ -2,14 +2,25 @@
 // mbarriers with bounded waits, TMA bulk and tensor copies, and the tcgen05
 // family (tensor-memory allocation, MMA issue/commit, tensor-memory loads).
 //
-// Every wait is bounded (WAIT_CYCLES): a kernel that gives up sets an error
+// Every wait is bounded (wait_cycles()): a kernel that gives up sets an error
 // word for the host instead of spinning forever.
 #pragma once
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace lqcd {
 
-constexpr long long WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
+// Bound of every device-side wait, in SM clock cycles (default about 2 s at
+// 2 GHz). Each translation unit that includes this header holds its own copy
+// on each device; set_wait_cycles_here() sets the copy of the including unit on
+// the current device (the C ABI's lqcd_set_wait_limit sets all of them).
+constexpr long long DEFAULT_WAIT_CYCLES = 4000000000ll;
+static __device__ long long g_wait_cycles = DEFAULT_WAIT_CYCLES;
+__device__ __forceinline__ long long wait_cycles() { return *(volatile long long*)&g_wait_cycles; }
+static inline cudaError_t set_wait_cycles_here(long long cycles) {
+    if (cycles <= 0) cycles = DEFAULT_WAIT_CYCLES;
+    return cudaMemcpyToSymbol(g_wait_cycles, &cycles, sizeof(cycles));
+}
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -33,11 +44,18 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for the phase of the given parity to complete, at most WAIT_CYCLES.
+// Wait for the phase of the given parity to complete, at most wait_cycles().
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    const long long t0 = clock64();
+    const long long t0 = clock64(), lim = wait_cycles();
     while (!mbar_test(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
+        if (clock64() - t0 > lim) return false;
+    return true;
+}
+// Wait for a device word to become nonzero, at most wait_cycles().
+__device__ __forceinline__ bool flag_wait(const volatile int* flag) {
+    const long long t0 = clock64(), lim = wait_cycles();
+    while (*flag == 0)
+        if (clock64() - t0 > lim) return false;
     return true;
 }
 

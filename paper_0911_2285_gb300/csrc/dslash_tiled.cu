@@ -280,4 +280,6 @@ cudaError_t launch_matvec_tiled(const Geom& g, const TileGeom& tg, const void* l
     return cudaGetLastError();
 }
 
+cudaError_t set_wait_cycles_tiled(long long cycles) { return set_wait_cycles_here(cycles); }
+
 }  // namespace lqcd

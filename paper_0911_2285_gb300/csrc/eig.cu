@@ -695,9 +695,12 @@ size_t eig_work_elems() {
 cudaError_t launch_small_eig(int n, const double2* A, int lda, int nsel, double2* lam, double2* Y, double2* Z,
                              int ldyz, int* info, double2* w, cudaStream_t st) {
     if (n < 1 || n > MAX_SMALL) return cudaErrorInvalidValue;
-    size_t sm = EigSmem::bytes(n);
-    cudaError_t e = set_smem((const void*)small_eig_kernel, sm);
+    // The kernel's shared-memory limit is only ever set to the largest size
+    // (bytes(MAX_SMALL)); a smaller per-call value would lower it for every
+    // other caller of this kernel, including the allocation-free entry point.
+    cudaError_t e = set_smem((const void*)small_eig_kernel, EigSmem::bytes(MAX_SMALL));
     if (e != cudaSuccess) return e;
+    const size_t sm = EigSmem::bytes(n);
     small_eig_kernel<<<1, ET, sm, st>>>(n, A, lda, nsel, lam, Y, Z, ldyz, w, info);
     count_launches(1);
     return cudaGetLastError();
@@ -706,8 +709,8 @@ cudaError_t launch_small_eig(int n, const double2* A, int lda, int nsel, double2
 cudaError_t launch_restart_coeffs_single(int m, int nev, const double2* H, int* r, double2* Yc, double2* Zc,
                                          double2* lam, int* info, double2* w, cudaStream_t st) {
     if (m < 3 || m > MAX_M || 2 * nev >= m || nev < 1) return cudaErrorInvalidValue;
-    size_t sm = EigSmem::bytes(m);
-    cudaError_t e = set_smem((const void*)restart_single_kernel, sm);
+    const size_t sm = EigSmem::bytes(m);
+    cudaError_t e = set_smem((const void*)restart_single_kernel, EigSmem::bytes(MAX_M));   // never lowered
     if (e != cudaSuccess) return e;
     restart_single_kernel<<<1, ET, sm, st>>>(m, nev, H, r, Yc, Zc, lam, w, info);
     count_launches(1);
@@ -775,6 +778,10 @@ cudaError_t launch_small_gemm(int n, int k, int m, const double2* A, int lda, in
 // keeps the last call's contents: the status word is cleared by each call, the
 // substitution vectors are fully rewritten before they are read. Calls whose
 // kernels overlap on the GPU (different streams, or host threads) race on it.
+// The per-device set-up (the array's address, the shared-memory limit) is kept
+// for the life of the process: a cudaDeviceReset between calls is not supported.
+// Every other launcher of the same kernel keeps its shared-memory limit at the
+// maximum, so no other call can lower it below what this entry point needs.
 namespace {
 
 constexpr int NOALLOC_MAX_N = MAX_SMALL;
@@ -823,11 +830,12 @@ extern "C" lqcd_status lqcd_small_eig_noalloc(int n, const double* C, double* ev
     int* info = reinterpret_cast<int*>(scratch + NOALLOC_SCRATCH);
     const int nsel = Y ? n : 0;
     if (cudaMemsetAsync(info, 0, sizeof(int), st) != cudaSuccess) return LQCD_ERR_CUDA;
+    (void)cudaGetLastError();   // an earlier, unrelated launch error is not this call's
     small_eig_kernel<<<1, ET, EigSmem::bytes(n), st>>>(n, reinterpret_cast<const double2*>(C), n, nsel,
                                                        reinterpret_cast<double2*>(evals), reinterpret_cast<double2*>(Y),
                                                        reinterpret_cast<double2*>(Z), n, scratch, info);
     count_launches(1);
-    if (cudaGetLastError() != cudaSuccess) return LQCD_ERR_CUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) { (void)cudaGetLastError(); return LQCD_ERR_CUDA; }
     int hinfo = 0;
     if (cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LQCD_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return LQCD_ERR_CUDA;

@@ -71,10 +71,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 // Bounded wait that also gives up once another role has aborted.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, unsigned parity, volatile int* abort) {
-    const long long t0 = clock64();
+    const long long t0 = clock64(), lim = wait_cycles();
     while (!mbar_test(bar, parity)) {
         if (*abort) return false;
-        if (clock64() - t0 > WAIT_CYCLES) { *abort = 1; return false; }
+        if (clock64() - t0 > lim) { *abort = 1; return false; }
     }
     return true;
 }
@@ -671,6 +671,23 @@ cudaError_t launch_dots_tc(int a, const void* X, size_t x_stride, int b, const v
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// ------------------------------------------------------------ bounded waits
+// One thread waits, with the same bounded wait as the copy pipelines above, for
+// a device word to become nonzero; status = 1 if the wait gave up.
+namespace {
+__global__ void flag_wait_kernel(const int* flag, int* status) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *status = flag_wait(flag) ? 0 : 1;
+}
+}  // namespace
+
+cudaError_t set_wait_cycles_tc(long long cycles) { return set_wait_cycles_here(cycles); }
+
+cudaError_t launch_flag_wait(const int* flag, int* status, cudaStream_t st) {
+    flag_wait_kernel<<<1, 32, 0, st>>>(flag, status);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace lqcd

@@ -139,4 +139,11 @@ cudaError_t launch_final_ritz(SlotState* st_, const SlotPtrs* ptrs, int slot, do
 cudaError_t launch_small_gemm(int n, int k, int m, const double2* A, int lda, int transA,
                               const double2* B, int ldb, double2* C, int ldc, cudaStream_t st);
 
+// Bound of the device-side waits (SM clock cycles) of the kernels of gemm_tc.cu
+// and dslash_tiled.cu on the current device; cycles <= 0 restores the default.
+cudaError_t set_wait_cycles_tc(long long cycles);
+cudaError_t set_wait_cycles_tiled(long long cycles);
+// One-thread kernel: bounded wait for *flag != 0; *status = 1 if it gave up.
+cudaError_t launch_flag_wait(const int* flag, int* status, cudaStream_t st);
+
 }  // namespace lqcd

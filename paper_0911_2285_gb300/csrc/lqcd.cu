@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -155,8 +156,14 @@ struct lqcd_ctx {
     std::vector<int> last_vs, last_restarts;
     int last_window_valid = 0;
 
+    // Host-side fault injection (LQCD_FAULT=alloc:N in the environment at init):
+    // the N-th device allocation of the context reports cudaErrorMemoryAllocation
+    // without allocating, to exercise the clean-up paths. Nothing runs on the GPU.
+    int fault_alloc = -1, n_alloc = 0;
+
     template <typename T> cudaError_t alloc(T** p, size_t bytes) {
         void* q = nullptr;
+        if (++n_alloc == fault_alloc) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
         if (e != cudaSuccess) return e;
         allocs.push_back(q);
@@ -268,6 +275,10 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     if (vs != LQCD_OK) return vs;
     lqcd_ctx* c = new lqcd_ctx();
     c->p = *params;
+    if (const char* f = getenv("LQCD_FAULT")) {
+        int n = 0;
+        if (sscanf(f, "alloc:%d", &n) == 1 && n > 0) c->fault_alloc = n;
+    }
     if (c->p.k_max == 0) c->p.k_max = MAX_SLOTS;
     if (c->p.delta == 0.0) c->p.delta = 0.01;
     c->kmax = c->p.k_max;
@@ -1543,5 +1554,34 @@ extern "C" lqcd_status lqcd_poll(lqcd_ctx* c, long long ticket, int* done, lqcd_
     if (info) *info = it->second.info;
     if (result) *result = it->second.status;
     c->finished.erase(it);
+    return LQCD_OK;
+}
+
+// ============================================================ bounded waits
+namespace {
+__device__ int g_flag_status;   // status word of lqcd_wait_flag
+}
+
+extern "C" lqcd_status lqcd_set_wait_limit(long long cycles) {
+    CK(set_wait_cycles_tc(cycles));
+    CK(set_wait_cycles_tiled(cycles));
+    return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_wait_flag(const int* flag, void* cuda_stream) {
+    if (!flag) return LQCD_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_flag_status));
+    int* status = reinterpret_cast<int*>(p);
+    CK(cudaMemsetAsync(status, 0, sizeof(int), st));
+    CK(launch_flag_wait(flag, status, st));
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h) {
+        g_last_error = "lqcd_wait_flag: the bounded wait gave up";
+        return LQCD_ERR_TIMEOUT;
+    }
     return LQCD_OK;
 }

@@ -113,6 +113,10 @@ def lib():
         L.lqcd_small_eig_noalloc.restype = C.c_int
         L.lqcd_apply_pair.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
         L.lqcd_apply_pair.restype = C.c_int
+        L.lqcd_set_wait_limit.argtypes = [C.c_longlong]
+        L.lqcd_set_wait_limit.restype = C.c_int
+        L.lqcd_wait_flag.argtypes = [vp, vp]
+        L.lqcd_wait_flag.restype = C.c_int
         L.lqcd_dslash_variant.argtypes = [vp]
         L.lqcd_dslash_variant.restype = C.c_int
         for name in ("lqcd_eigbicg_init", "lqcd_solve", "lqcd_deflate", "lqcd_eigs", "lqcd_apply",
@@ -157,11 +161,19 @@ def _ptr(a, n_expected=None):
 
 
 def _fingerprint(a):
-    """Short digest of a gauge field (shape and a strided sample), to refuse an
-    eigenspace saved for another field."""
-    flat = a.reshape(-1)
-    sample = np.ascontiguousarray(flat[:: max(1, flat.size // 65536)])
-    return hashlib.sha256(repr(a.shape).encode() + sample.tobytes()).hexdigest()[:32]
+    """Digest of a whole gauge field (shape and every link entry), to refuse an
+    eigenspace saved for another field. Hashes the contiguous buffer once per
+    context (about a second at 24^3x64)."""
+    a = np.ascontiguousarray(a)
+    h = hashlib.sha256(repr(a.shape).encode())
+    h.update(a.reshape(-1).view(np.uint8))
+    return h.hexdigest()[:32]
+
+
+def _npz_path(path):
+    """``np.savez`` appends ``.npz`` to a path without it; use the same name on load."""
+    path = os.fspath(path)
+    return path if path.endswith(".npz") else path + ".npz"
 
 
 class Solver:
@@ -359,21 +371,31 @@ class Solver:
         """Checkpoint the accumulated eigenspace (U_r, U_l and H = U_l^H A U_r) with
         the lattice, kappa and a digest of the gauge field, as an ``.npz`` file."""
         ur, ul, h = self.eigspace_get()
-        np.savez(path, Ur=ur, Ul=ul, H=h, dims=np.array(self.dims), kappa=np.float64(self.kappa),
+        np.savez(_npz_path(path), Ur=ur, Ul=ul, H=h, dims=np.array(self.dims), kappa=np.float64(self.kappa),
                  links_fp=np.array(self._links_fp))
 
     def load_eigenspace(self, path):
         """Resume from :meth:`save_eigenspace`: the vectors are installed and H is
         recomputed on this context's operator (which must be the same gauge field,
         lattice and kappa, else ``ValueError``). The loaded vectors count as complete
-        eigBiCG solves for AUTO mode."""
-        with np.load(path) as d:
+        eigBiCG solves for AUTO mode. The recomputed H must agree with the stored
+        one to ``h_rtol`` of its largest entry (FP32-stored vectors: their projections
+        are FP32 sums; FP64: rounding), else ``ValueError``. Returns the largest
+        relative difference."""
+        with np.load(_npz_path(path)) as d:
             if tuple(int(x) for x in d["dims"]) != self.dims or float(d["kappa"]) != self.kappa:
                 raise ValueError("eigenspace saved for another lattice or kappa")
             if str(d["links_fp"]) != self._links_fp:
                 raise ValueError("eigenspace saved for another gauge field")
-            ur, ul = d["Ur"], d["Ul"]
+            ur, ul, h_saved = d["Ur"], d["Ul"], d["H"]
         self.eigspace_set(ur, ul)
+        _, _, h = self.eigspace_get()
+        scale = max(float(np.abs(h_saved).max()) if h_saved.size else 0.0, 1e-300)
+        diff = float(np.abs(h - h_saved).max()) / scale if h.size else 0.0
+        h_rtol = 1e-4 if self.precision in ("mixed", MIXED) else 1e-10
+        if diff > h_rtol:
+            raise ValueError(f"recomputed H differs from the stored one by {diff:.3g} (relative)")
+        return diff
 
     def last_window(self, slot=0):
         m = self.params.m

@@ -57,3 +57,16 @@ def test_init_rejects_bad_parameters_without_touching_the_device(libpath, bad):
     with pytest.raises(L.LQCDError) as e:
         L.Solver(links if v > 0 else links, dims, **args)
     assert e.value.status == L.ERR_ARG
+
+
+def test_init_refuses_a_plan_above_the_hbm_budget_without_touching_the_device(libpath):
+    """The memory plan is checked against hbm_budget_bytes before any device call."""
+    import numpy as np
+    from paper_0911_2285_gb300 import lqcd as L
+    dims = (8, 8, 8, 8)
+    links = np.zeros(int(np.prod(dims)) * 36, dtype=np.complex128)
+    with pytest.raises(L.LQCDError) as e:
+        L.Solver(links, dims, 0.12, nev=8, m=24, tol=1e-10, precision="mixed", k_max=8,
+                 hbm_budget_bytes=64 << 20)
+    assert e.value.status == L.ERR_OOM
+    assert "budget" in L.last_error()
