@@ -85,11 +85,30 @@ typedef struct {
     int maxiter;              /* BiCG iterations per source */
     lqcd_precision precision;
     double deftol;            /* DefTol of Alg. Incremental; 0 disables the re-deflation restart */
-    int k_max;                /* right-hand sides per batched launch (1..8); 0 = 8 */
-    size_t hbm_budget_bytes;  /* 0 = no limit; init fails with LQCD_ERR_OOM above it */
+    int k_max;                /* right-hand sides per batched launch (1..8); 0 = autotuned: init
+                                 times one BiCG iteration on 1, 2, 4 and 8 slots and keeps the
+                                 batch size with the most right-hand sides per second */
+    size_t hbm_budget_bytes;  /* device memory the context may hold; 0 = whatever is free.
+                                 Init fails with LQCD_ERR_OOM when the fixed plan (links,
+                                 batch slots, eigenspace, scratch) exceeds it; each eigBiCG
+                                 window (2 (m+1) Krylov fields) is allocated when a source
+                                 starts eigBiCG and only if it fits: see lqcd_solve and
+                                 lqcd_progress */
     int n_def_max;            /* eigenspace capacity in vectors (<= 80); 0 = min(80, n1*nev) */
     double delta;             /* MIXED reliable update when ||r|| < delta * ||r at the last update||
                                  (or < 1e-3 * max||r|| since then); 0 = 0.01 */
+    int gamma5;               /* 1 = the gamma5-Hermitian variant of Sec. 4 (A^+ = gamma5 A gamma5):
+                                 shadow start rhat_0 = gamma5 r_0, so rhat_j = gamma5 r_j and
+                                 phat_j = gamma5 p_j are never stored and A^+ phat = gamma5 A p:
+                                 one operator product per BiCG iteration, real scalars; the
+                                 eigBiCG window's left vectors are gamma5 images of the right
+                                 ones.  0 = general two-sided BiCG with rhat_0 = r_0. */
+    int bicgstab;             /* 1 = phase 2 as the paper runs it (Alg. Incremental eigBiCG,
+                                 step 3): DEFLATED and PLAIN solves use BiCGStab (shadow
+                                 rhat = r_0, two products with A per step, none with A^+),
+                                 with the same reliable updates and DefTol restart; eigBiCG
+                                 and its correction leg stay BiCG.  0 = BiCG throughout.
+                                 Not combinable with gamma5. */
 } lqcd_params;
 
 typedef struct {
@@ -125,7 +144,14 @@ lqcd_status lqcd_eigbicg_init(lqcd_ctx **ctx, const lqcd_params *params,
  * deftol > 0 one re-deflation restart at ||r|| < deftol ||b|| (phase 2).
  * info: k entries (may be NULL).  k may exceed k_max: the sources are then
  * processed in consecutive batches of k_max (for continuous refill of freed
- * slots use the serving session below).
+ * slots use the serving session below).  An eigBiCG batch holds one window per
+ * source, allocated for as many sources as the memory plan admits (the batch
+ * shrinks to fit; LQCD_ERR_OOM if not even one window fits) and released when
+ * the batch's Ritz vectors have joined the eigenspace.  In MIXED precision an
+ * eigBiCG source runs in two legs: the windowed iteration without reliable
+ * updates (which would break the window's Lanczos relation) to the recursive
+ * tolerance, then, after its Ritz vectors joined the eigenspace, a deflated
+ * correction leg from the FP64 residual with reliable updates (outer_steps = 1).
  * Returns LQCD_ERR_NOCONV / LQCD_ERR_BREAKDOWN if any source failed; x then
  * holds the best iterate. */
 lqcd_status lqcd_solve(lqcd_ctx *ctx, int k, const double *b, double *x,
@@ -136,6 +162,13 @@ lqcd_status lqcd_solve(lqcd_ctx *ctx, int k, const double *b, double *x,
  * the other slots keep iterating; the gauge field and the eigenspace stay
  * resident.  The mode is resolved at admission (AUTO: eigBiCG while fewer than
  * n1 sources have fed or are feeding the eigenspace, deflated BiCG after).
+ * Admission is by device memory: an eigBiCG request also needs a window, which
+ * is allocated only if it fits the memory plan (hbm_budget_bytes, else the free
+ * device memory less 1 GiB); a request that does not fit waits in the queue and
+ * is admitted when a window is released, while later requests that need no
+ * window are admitted past it.  When no window is held (none will be released),
+ * an AUTO request runs deflated BiCG instead and an explicit EIGBICG request
+ * finishes with LQCD_ERR_OOM.
  * The context must not run lqcd_solve while requests are in flight
  * (LQCD_ERR_STATE).
  *
@@ -180,6 +213,21 @@ lqcd_status lqcd_eigs(lqcd_ctx *ctx, int *n_inout, double *evals,
  * (LQCD_FP64 or LQCD_MIXED = FP32 operator on FP32-rounded input).  k fields. */
 lqcd_status lqcd_apply(lqcd_ctx *ctx, int dagger, lqcd_precision prec, int k,
                        const double *in, double *out, int on_device);
+
+/* Device memory of the context: *plan_bytes = the fixed plan (allocated at init),
+ * *window_bytes = one eigBiCG window, *windows_attached = windows held now.
+ * Any output may be NULL. */
+lqcd_status lqcd_memory_info(const lqcd_ctx *ctx, size_t *plan_bytes, size_t *window_bytes,
+                             int *windows_attached);
+
+/* Right-hand sides per batched launch: k_max, or the autotuned size (k_max = 0). */
+int lqcd_batch_size(const lqcd_ctx *ctx);
+
+/* Measurement hook: ms[k] (k = 0..8) = device time of one BiCG iteration
+ * (operator kernel, residual update, direction update) over k slots as the
+ * batch-size autotuner measured it (0 where not timed).  LQCD_ERR_STATE if the
+ * context was created with k_max > 0 (no autotuning). */
+lqcd_status lqcd_batch_timings(const lqcd_ctx *ctx, double *ms);
 
 /* Size of the eigenspace (number of right/left vector pairs). */
 int lqcd_eigspace_size(const lqcd_ctx *ctx);

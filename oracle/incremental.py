@@ -112,12 +112,18 @@ class IncrementalResult:
     ritz: list = field(default_factory=list)
 
 
-def deflated_bicg(op, space, b, x0=None, tol=1e-10, deftol=0.0, maxiter=10000):
+def _shadow(op, b, x, gamma5):
+    """Shadow start of a BiCG run from x: ``r_0`` (general) or ``gamma5 r_0`` (Sec. 4)."""
+    return op.gamma5(b - op.apply(x)) if gamma5 else None
+
+
+def deflated_bicg(op, space, b, x0=None, tol=1e-10, deftol=0.0, maxiter=10000, gamma5=False):
     """Phase-2 solve: deflate the initial guess and run BiCG.
 
     With ``tol < deftol`` the solve stops once at ``deftol ||b||``, re-deflates
     the current iterate and restarts BiCG to ``tol`` (the paper's DefTol
-    restart read as one restart at the ``DefTol`` crossing).
+    restart read as one restart at the ``DefTol`` crossing). ``gamma5``: the
+    shadow start of each BiCG run is ``gamma5 r_0`` (Sec. 4).
     """
     b = np.asarray(b, dtype=np.complex128)
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128)
@@ -125,11 +131,11 @@ def deflated_bicg(op, space, b, x0=None, tol=1e-10, deftol=0.0, maxiter=10000):
     iters = 0
     mv = 0
     if deftol > tol:
-        res = bicg(op, b, x, tol=deftol, maxiter=maxiter)
+        res = bicg(op, b, x, tol=deftol, maxiter=maxiter, rhat0=_shadow(op, b, x, gamma5))
         iters += res.iters
         mv += res.matvecs
         x = deflate(op, space, b, res.x)
-    res = bicg(op, b, x, tol=tol, maxiter=maxiter - iters)
+    res = bicg(op, b, x, tol=tol, maxiter=maxiter - iters, rhat0=_shadow(op, b, x, gamma5))
     return res.x, iters + res.iters, mv + res.matvecs, res.true_resid
 
 
@@ -154,8 +160,10 @@ def deflated_bicgstab(op, space, b, x0=None, tol=1e-10, deftol=0.0, maxiter=1000
 
 
 def incremental_eigbicg(op, sources, nev, m, n1, tol=1e-10, deftol=0.0, maxiter=10000,
-                        x0s=None):
-    """Algorithm Incremental eigBiCG over a list of right-hand sides (sequential)."""
+                        x0s=None, gamma5=False):
+    """Algorithm Incremental eigBiCG over a list of right-hand sides (sequential).
+    ``gamma5``: every BiCG run starts its shadow sequence at ``gamma5 r_0`` (the
+    gamma5-Hermitian variant of Sec. 4)."""
     space = Eigenspace(op.n)
     out = IncrementalResult()
     for k, b in enumerate(sources):
@@ -164,7 +172,7 @@ def incremental_eigbicg(op, sources, nev, m, n1, tol=1e-10, deftol=0.0, maxiter=
         mv0 = op.matvecs
         if k < n1:
             x0 = deflate(op, space, b, x0)
-            res = eigbicg(op, b, nev, m, x0=x0, tol=tol, maxiter=maxiter)
+            res = eigbicg(op, b, nev, m, x0=x0, tol=tol, maxiter=maxiter, rhat0=_shadow(op, b, x0, gamma5))
             space = grow(op, space, res.U, res.Q)
             out.x.append(res.x)
             out.iters.append(res.iters)
@@ -172,7 +180,7 @@ def incremental_eigbicg(op, sources, nev, m, n1, tol=1e-10, deftol=0.0, maxiter=
             out.modes.append("eigbicg")
             out.ritz.append(res.evals)
         else:
-            x, it, _, tr = deflated_bicg(op, space, b, x0, tol=tol, deftol=deftol, maxiter=maxiter)
+            x, it, _, tr = deflated_bicg(op, space, b, x0, tol=tol, deftol=deftol, maxiter=maxiter, gamma5=gamma5)
             out.x.append(x)
             out.iters.append(it)
             out.true_resid.append(tr)

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, 1)
     const int seg = bid / Lz;
     SlotState& st = states[slot];
     const SlotPtrs& P = ptrs[slot];
-    if (st.status != ST_RUNNING) return;
+    if (st.status != ST_RUNNING || st.stab) return;
     const int par = st.iter & 1;
     const float4* src[2] = {reinterpret_cast<const float4*>(P.p), reinterpret_cast<const float4*>(P.phat)};
     float4* dst[2] = {reinterpret_cast<float4*>(P.Ap[par]), reinterpret_cast<float4*>(P.Ahp[par])};

@@ -656,6 +656,93 @@ __global__ void lu_solve_kernel(int n, const double2* LU, int lda, const int* pi
     }
 }
 
+// One factor of P A = L U applied to B (n x nrhs, or nrows x n for LU_RIGHT_U),
+// one thread per column (per row for LU_RIGHT_U):
+//   LU_LEFT_PL : B <- L^{-1} P B        LU_LEFT_U : B <- U^{-1} B
+//   LU_RIGHT_U : B <- B U^{-1}          LU_LEFT_LH: B <- P^T L^{-H} B
+__global__ void lu_part_kernel(int n, const double2* LU, int lda, const int* piv, int part, int ncols, double2* B,
+                               int ldb) {
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+        if (part == LU_LEFT_PL) {
+            for (int k = 0; k < n; ++k) {
+                const int p = piv[k];
+                if (p != k) { double2 t = B[k * ldb + c]; B[k * ldb + c] = B[p * ldb + c]; B[p * ldb + c] = t; }
+            }
+            for (int i = 0; i < n; ++i) {
+                double2 acc = B[i * ldb + c];
+                for (int j = 0; j < i; ++j) acc = acc - LU[i * lda + j] * B[j * ldb + c];
+                B[i * ldb + c] = acc;
+            }
+        } else if (part == LU_LEFT_U) {
+            for (int i = n - 1; i >= 0; --i) {
+                double2 acc = B[i * ldb + c];
+                for (int j = i + 1; j < n; ++j) acc = acc - LU[i * lda + j] * B[j * ldb + c];
+                B[i * ldb + c] = cdiv(acc, LU[i * lda + i]);
+            }
+        } else if (part == LU_RIGHT_U) {   // row c: x U = b, x_j = (b_j - sum_{i<j} x_i U_ij) / U_jj
+            double2* row = B + (size_t)c * ldb;
+            for (int j = 0; j < n; ++j) {
+                double2 acc = row[j];
+                for (int i = 0; i < j; ++i) acc = acc - row[i] * LU[i * lda + j];
+                row[j] = cdiv(acc, LU[j * lda + j]);
+            }
+        } else {   // LU_LEFT_LH: L^H w = b (unit upper), then x = P^T w
+            for (int i = n - 1; i >= 0; --i) {
+                double2 acc = B[i * ldb + c];
+                for (int j = i + 1; j < n; ++j) acc = acc - conj_(LU[j * lda + i]) * B[j * ldb + c];
+                B[i * ldb + c] = acc;
+            }
+            for (int k = n - 1; k >= 0; --k) {
+                const int p = piv[k];
+                if (p != k) { double2 t = B[k * ldb + c]; B[k * ldb + c] = B[p * ldb + c]; B[p * ldb + c] = t; }
+            }
+        }
+    }
+}
+
+// Rank-revealing selection on a small square block B (n <= 32, row-major, ld):
+// LU with complete pivoting on a copy, stopped at the first pivot below
+// tau * |first pivot|. out[0] = r (pivots kept), out[1 + i] = row index of pivot
+// i, out[1 + n + i] = its column index (i < r). One thread.
+__global__ void pivot_select_kernel(int n, const double2* B, int ld, double tau, int* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double2 a[32][32];
+    int rows[32], cols[32];
+    for (int i = 0; i < n; ++i) {
+        rows[i] = cols[i] = i;
+        for (int j = 0; j < n; ++j) a[i][j] = B[i * ld + j];
+    }
+    double p0 = 0.0;
+    int r = 0;
+    for (int k = 0; k < n; ++k) {
+        int pi = k, pj = k;
+        double best = -1.0;
+        for (int i = k; i < n; ++i)
+            for (int j = k; j < n; ++j) {
+                const double v = cabs2(a[i][j]);
+                if (v > best) { best = v; pi = i; pj = j; }
+            }
+        best = sqrt(best);
+        if (k == 0) p0 = best;
+        if (!(best > tau * p0) || best == 0.0) break;
+        if (pi != k) {
+            for (int j = 0; j < n; ++j) { double2 t = a[k][j]; a[k][j] = a[pi][j]; a[pi][j] = t; }
+            int t = rows[k]; rows[k] = rows[pi]; rows[pi] = t;
+        }
+        if (pj != k) {
+            for (int i = 0; i < n; ++i) { double2 t = a[i][k]; a[i][k] = a[i][pj]; a[i][pj] = t; }
+            int t = cols[k]; cols[k] = cols[pj]; cols[pj] = t;
+        }
+        for (int i = k + 1; i < n; ++i) {
+            const double2 l = cdiv(a[i][k], a[k][k]);
+            for (int j = k + 1; j < n; ++j) a[i][j] = a[i][j] - l * a[k][j];
+        }
+        r = k + 1;
+    }
+    out[0] = r;
+    for (int i = 0; i < n; ++i) { out[1 + i] = rows[i]; out[1 + n + i] = cols[i]; }
+}
+
 __global__ void small_gemm_kernel(int n, int k, int m, const double2* A, int lda, int transA,
                                   const double2* B, int ldb, double2* C, int ldc) {
     for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < n * m; e += blockDim.x * gridDim.x) {
@@ -748,6 +835,20 @@ cudaError_t launch_lu_factor(int n, double2* A, int lda, int* piv, int* info, cu
 cudaError_t launch_lu_solve(int n, const double2* LU, int lda, const int* piv, int trans, int nrhs, double2* B,
                             int ldb, cudaStream_t st) {
     lu_solve_kernel<<<1, 128, 0, st>>>(n, LU, lda, piv, trans, nrhs, B, ldb);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lu_part(int n, const double2* LU, int lda, const int* piv, int part, int ncols, double2* B,
+                           int ldb, cudaStream_t st) {
+    lu_part_kernel<<<1, 128, 0, st>>>(n, LU, lda, piv, part, ncols, B, ldb);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pivot_select(int n, const double2* B, int ld, double tau, int* out, cudaStream_t st) {
+    if (n < 1 || n > 32) return cudaErrorInvalidValue;
+    pivot_select_kernel<<<1, 32, 0, st>>>(n, B, ld, tau, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -262,8 +262,46 @@ template <> struct Unit<double> {
     }
 };
 
-// Start: r0 = b - A x_hi (already in r_true, FP64), rhat0 = r0, p = r, phat = rhat,
-// x_lo = 0; rho_0 = (rhat_0, r_0), ||r_0||, ||b||  (Algorithm eigBiCG, steps 1-2).
+// Compensated FP32 accumulation of a complex sum (Knuth's two-sum per term), for
+// the gamma5 variant's inner products rho = r^H gamma5 r and sigma = p^H gamma5 A p:
+// their terms have both signs and cancel down to about ||r||^2 / sqrt(N), so a
+// plain FP32 sum would lose three to four digits of them. The per-thread value
+// goes to FP64 block and cross-block sums.
+struct CompC {
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+    __device__ __forceinline__ static void add1(float& s, float& c, float v) {
+        const float t = s + v, bp = t - s;
+        c += (s - (t - bp)) + (v - bp);
+        s = t;
+    }
+    __device__ __forceinline__ void add(float2 v) { add1(sx, cx, v.x); add1(sy, cy, v.y); }
+    __device__ __forceinline__ double2 value() const { return make_double2((double)sx + cx, (double)sy + cy); }
+};
+
+// Block and cross-block sum of (z, (a, b)) per slot: in the storage precision,
+// or (gamma5 variant with FP32 storage, compensated z) in FP64 throughout.
+template <typename S>
+__device__ __forceinline__ bool reduce2(const SlotPtrs& P, int kind, bool comp, const CompC& cz, const Acc<S>& acc,
+                                        double2 (&tot)[2], unsigned nblocks, unsigned bid) {
+    if (comp) {
+        double2 v[2] = {cz.value(), make_double2((double)acc.a, (double)acc.b)};
+        return reduce_slot<2>(P, kind, v, tot, nblocks, bid);
+    }
+    cplx<S> v[2];
+    acc.to(v);
+    return reduce_slot<2>(P, kind, v, tot, nblocks, bid);
+}
+
+// gamma5 = diag(1, 1, -1, -1) on a vector unit: units u < N/4 hold spins 0 and 1
+// (chunks q = 0..2 of the field layout), the rest spins 2 and 3.
+template <typename S> __device__ __forceinline__ Unit<S> g5u(Unit<S> v, size_t u, size_t N) {
+    if (u >= N / 4) { v.a = -v.a; v.b = -v.b; }
+    return v;
+}
+
+// Start: r0 = b - A x_hi (already in r_true, FP64), rhat0 = r0 (gamma5 r0 in the
+// gamma5 variant), p = r, phat = rhat, x_lo = 0; rho_0 = (rhat_0, r_0), ||r_0||,
+// ||b||  (Algorithm eigBiCG, steps 1-2).
 template <typename S>
 __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
     SlotState& st = states[blockIdx.y];
@@ -273,6 +311,8 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
         for (int e = threadIdx.x; e < st.m * st.m; e += blockDim.x) P.H[e] = make_double2(0.0, 0.0);
     using C = cplx<S>;
     Acc<S> acc;   // rho, |r|^2, |b|^2
+    CompC cz;     // rho of the gamma5 variant (FP32 storage)
+    const bool comp = st.g5 && sizeof(S) == 4;
     const size_t units = N / 2;
     Unit<S> zero{mk<S>(0, 0), mk<S>(0, 0)};
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
@@ -280,18 +320,26 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
         Unit<double> bb = Unit<double>::load(P.b, u);
         Unit<S> r{cvt<S>(rt.a), cvt<S>(rt.b)};
         r.store(P.V, u);
-        r.store(P.W, u);
         r.store(P.p, u);
-        r.store(P.phat, u);
+        Unit<S> h = r;
+        if (st.g5) {   // rhat0 = gamma5 r0: only the window keeps it
+            h = g5u(r, u, N);
+            if (st.m > 0) h.store(P.W, u);
+        } else {
+            r.store(P.W, u);
+            r.store(P.phat, u);
+        }
         zero.store(P.x_lo, u);
-        acc.z = acc.z + cdot(r.a, r.a) + cdot(r.b, r.b);
+        if (comp) {
+            if constexpr (sizeof(S) == 4) { cz.add(cdot(h.a, r.a)); cz.add(cdot(h.b, r.b)); }
+        } else {
+            acc.z = acc.z + cdot(h.a, r.a) + cdot(h.b, r.b);
+        }
         acc.a += abs2(r.a) + abs2(r.b);
         acc.b += (S)(cabs2(bb.a) + cabs2(bb.b));
     }
-    cplx<S> v[2];
-    acc.to(v);
     double2 tot[2];
-    if (reduce_slot<2>(P, CNT_START, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+    if (reduce2<S>(P, CNT_START, comp, cz, acc, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
         st.rho = tot[0];
         st.rnorm = sqrt(tot[1].x);
         st.bnorm = sqrt(tot[1].y);
@@ -303,6 +351,9 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
         st.matvecs = 1; st.live = 1;
         st.alpha_prev = make_double2(0, 0); st.beta_prev = make_double2(0, 0);
         if (st.rnorm <= st.tol * st.bnorm) { st.status = ST_CONVERGED; st.live = 0; }
+        // rho_0 = (rhat_0, r_0) must not vanish (e.g. the gamma5 shadow start on a
+        // source whose upper and lower spin halves have equal norms)
+        else if (!(cabs_(st.rho) >= BREAK_TOL * st.rhat_norm * st.rnorm)) { st.status = ST_BREAKDOWN; st.live = 0; }
     }
     (void)sizeof(C);
 }
@@ -336,7 +387,10 @@ template <int THREADS, int BZ> struct SiteMap {
     }
 };
 
-template <typename S, int THREADS, int MINB, bool PAIR, int BZ = 0>
+//   G5   = true : the gamma5 variant (Sec. 4): one job per slot, A p only, with
+//                 phat = gamma5 p formed in registers for sigma; windowed slots
+//                 also store A^+ phat = gamma5 A p for the restart's coupling.
+template <typename S, int THREADS, int MINB, bool PAIR, int BZ = 0, bool G5 = false>
 __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const void* links, double kappa,
                                                                SlotState* states, const SlotPtrs* ptrs,
                                                                int njobs) {
@@ -345,15 +399,16 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
     // each block takes a contiguous run of site units (neighbouring sites stay on one SM)
     const int per = (map.nunits + nsb - 1) / nsb;
     const int u0 = sblock * per, u1 = min(map.nunits, u0 + per);
-    const int slot = PAIR ? job : job >> 1, which = PAIR ? 0 : job & 1;
+    const int slot = (PAIR || G5) ? job : job >> 1, which = (PAIR || G5) ? 0 : job & 1;
     SlotState& st = states[slot];
     const SlotPtrs& P = ptrs[slot];
-    if (st.status != ST_RUNNING) return;
+    if (st.status != ST_RUNNING || st.stab) return;   // BiCGStab slots run their own kernels
     using C = cplx<S>;
     const int par = st.iter & 1;
     typename LinkSel<S>::type U{reinterpret_cast<decltype(U.u)>(links), g.V};
     const S k = (S)kappa;
     Acc<S> sacc;   // sigma, |phat|^2, |Ap|^2
+    CompC scomp;   // sigma of the gamma5 variant (FP32)
     if (PAIR) {
         FieldIn<S> inp{P.p, g.V}, inh{P.phat, g.V};
         for (int u = u0; u < u1; ++u) {
@@ -378,6 +433,7 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
     } else {
         FieldIn<S> in{which ? P.phat : P.p, g.V};
         void* out = which ? P.Ahp[par] : P.Ap[par];
+        const bool win = G5 && st.m > 0;
         for (int u = u0; u < u1; ++u) {
             const int s = map.site(g, u);
             if (s < 0) continue;
@@ -385,10 +441,25 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
             if (which) hop_site<true, S>(g, U, in, s, acc);
             else hop_site<false, S>(g, U, in, s, acc);
             in.load(s, self);
+            const C (&self_p)[12] = self;
 #pragma unroll
             for (int c = 0; c < 12; ++c) acc[c] = self[c] - k * acc[c];
             Field<S>::store(out, g.V, s, acc);
-            if (!which) {
+            if (G5) {   // phat = gamma5 p: spins 0, 1 (c < 6) keep their sign
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const C ph = c < 6 ? self_p[c] : -self_p[c];
+                    if constexpr (sizeof(S) == 4) scomp.add(cdot(ph, acc[c]));
+                    else sacc.z = sacc.z + cdot(ph, acc[c]);
+                    sacc.a += abs2(ph);
+                    sacc.b += abs2(acc[c]);
+                }
+                if (win) {
+#pragma unroll
+                    for (int c = 6; c < 12; ++c) acc[c] = -acc[c];
+                    Field<S>::store(P.Ahp[par], g.V, s, acc);
+                }
+            } else if (!which) {
                 C ph[12];
                 Field<S>::load(P.phat, g.V, s, ph);
 #pragma unroll
@@ -401,14 +472,12 @@ __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const voi
         }
         if (which) return;
     }
-    cplx<S> v[2];
-    sacc.to(v);
     double2 tot[2];
-    if (reduce_slot<2>(P, CNT_MATVEC, v, tot, nsb, sblock) && threadIdx.x == 0) {
+    if (reduce2<S>(P, CNT_MATVEC, G5 && sizeof(S) == 4, scomp, sacc, tot, nsb, sblock) && threadIdx.x == 0) {
         st.sigma = tot[0];
         st.phat_norm = sqrt(tot[1].x);
         st.ap_norm = sqrt(tot[1].y);
-        st.matvecs += 2;
+        st.matvecs += G5 ? 1 : 2;   // the gamma5 variant applies A only
         if (!(cabs_(st.sigma) >= BREAK_TOL * st.phat_norm * st.ap_norm) || cabs2(st.sigma) == 0.0) {
             st.status = ST_BREAKDOWN;
         } else {
@@ -437,7 +506,7 @@ __global__ void __launch_bounds__(32 * JPB, MINB)
     const int ngroups = (g.V + 31) >> 5;
     LinksF U{reinterpret_cast<const float4*>(links), g.V};
     Acc<float> sacc;
-    if (job < njobs && states[slot].status == ST_RUNNING) {
+    if (job < njobs && states[slot].status == ST_RUNNING && !states[slot].stab) {
         const SlotState& st = states[slot];
         const SlotPtrs& P = ptrs[slot];
         const int par = st.iter & 1;
@@ -479,7 +548,7 @@ __global__ void __launch_bounds__(32 * JPB, MINB)
     if (!last_block(ptrs[0].counters + CNT_GROUP, gridDim.x * gridDim.y)) return;
     for (int sl = warp; sl < nslots; sl += JPB) {
         SlotState& st = states[sl];
-        if (st.status != ST_RUNNING) continue;
+        if (st.status != ST_RUNNING || st.stab) continue;
         const double2* pp = ptrs[sl].partials + (size_t)CNT_MATVEC * PARTIAL_STRIDE;
         double2 z = make_double2(0.0, 0.0), ab = make_double2(0.0, 0.0);
         for (int b = lane; b < (int)gridDim.x; b += 32) {
@@ -510,7 +579,7 @@ template <typename S>
 __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
     SlotState& st = states[blockIdx.y];
     const SlotPtrs& P = ptrs[blockIdx.y];
-    if (st.status != ST_RUNNING) return;
+    if (st.status != ST_RUNNING || st.stab) return;   // BiCGStab slots run their own kernels
     using C = cplx<S>;
     const int par = st.iter & 1;
     const C al = cvt<S>(st.alpha), alc = conj_(al);
@@ -521,22 +590,37 @@ __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, c
     const void* ap = P.Ap[par];
     const void* ahp = P.Ahp[par];
     Acc<S> acc;   // rho_j, |r_j|^2, |rhat_j|^2
+    CompC cz;     // rho_j of the gamma5 variant (FP32 storage)
+    const bool comp = st.g5 && sizeof(S) == 4;
     const size_t units = N / 2;
-    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
-        Unit<S> r = Unit<S>::load(rin, u), a = Unit<S>::load(ap, u);
-        Unit<S> h = Unit<S>::load(hin, u), ah = Unit<S>::load(ahp, u);
-        r.a = r.a - al * a.a; r.b = r.b - al * a.b;
-        h.a = h.a - alc * ah.a; h.b = h.b - alc * ah.b;
-        r.store(rout, u);
-        h.store(hout, u);
-        acc.z = acc.z + cdot(h.a, r.a) + cdot(h.b, r.b);
-        acc.a += abs2(r.a) + abs2(r.b);
-        acc.b += abs2(h.a) + abs2(h.b);
+    if (st.g5) {   // rhat_j = gamma5 r_j: one vector update, the window keeps gamma5 r_j
+        const bool win = st.m > 0;
+        for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+            Unit<S> r = Unit<S>::load(rin, u), a = Unit<S>::load(ap, u);
+            r.a = r.a - al * a.a; r.b = r.b - al * a.b;
+            r.store(rout, u);
+            const Unit<S> h = g5u(r, u, N);
+            if (win) h.store(hout, u);
+            if constexpr (sizeof(S) == 4) { cz.add(cdot(h.a, r.a)); cz.add(cdot(h.b, r.b)); }
+            else acc.z = acc.z + cdot(h.a, r.a) + cdot(h.b, r.b);
+            acc.a += abs2(r.a) + abs2(r.b);
+        }
+        acc.b = acc.a;
+    } else {
+        for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+            Unit<S> r = Unit<S>::load(rin, u), a = Unit<S>::load(ap, u);
+            Unit<S> h = Unit<S>::load(hin, u), ah = Unit<S>::load(ahp, u);
+            r.a = r.a - al * a.a; r.b = r.b - al * a.b;
+            h.a = h.a - alc * ah.a; h.b = h.b - alc * ah.b;
+            r.store(rout, u);
+            h.store(hout, u);
+            acc.z = acc.z + cdot(h.a, r.a) + cdot(h.b, r.b);
+            acc.a += abs2(r.a) + abs2(r.b);
+            acc.b += abs2(h.a) + abs2(h.b);
+        }
     }
-    cplx<S> v[2];
-    acc.to(v);
     double2 tot[2];
-    if (reduce_slot<2>(P, CNT_UPDATE, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+    if (reduce2<S>(P, CNT_UPDATE, comp, cz, acc, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
         st.rho_new = tot[0];
         st.rnorm_new = sqrt(tot[1].x);
         st.rhat_norm = sqrt(tot[1].y);
@@ -547,8 +631,14 @@ __global__ void __launch_bounds__(BL_THREADS) update_kernel(SlotState* states, c
             // Reliable update (FP32 Krylov vectors): when the residual has dropped by
             // delta since the last update, or far below the largest residual seen
             // since then (the recursion's rounding error scales with that maximum);
-            // and always to confirm convergence.
-            if (st.rnorm_new <= st.tol * st.bnorm) st.need_ru = 1;
+            // and always to confirm convergence. A slot with rec_stop set (the
+            // eigBiCG leg of a mixed-precision solve) never replaces r, which
+            // would break the Lanczos relation of its window, and stops at the
+            // first recursive convergence candidate instead.
+            if (st.rnorm_new <= st.tol * st.bnorm) {
+                if (st.rec_stop) st.status = ST_CONVERGED;
+                else st.need_ru = 1;
+            }
             if (st.rnorm_new > st.rmax) st.rmax = st.rnorm_new;
             if (st.delta > 0.0 && (st.rnorm_new < st.delta * st.r_ru || st.rnorm_new < 1e-3 * st.rmax)) st.need_ru = 1;
         }
@@ -732,21 +822,40 @@ __global__ void __launch_bounds__(BL_THREADS) replace_kernel(SlotState* states, 
     if (!st.live || !st.need_ru || (st.status != ST_RUNNING && st.status != ST_CONVERGED)) return;
     const bool run = st.status == ST_RUNNING;
     void* rcur = slot_field<S>(P.V, next_slot(st), N);
-    const void* hcur = slot_field<S>(P.W, next_slot(st), N);
+    void* hcur = slot_field<S>(P.W, next_slot(st), N);
     cplx<S> rho = mk<S>(S(0), S(0));
+    CompC cz;   // gamma5 variant, FP32 storage
+    const bool comp = st.g5 && sizeof(S) == 4;
     const size_t units = N / 2;
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
         if (run) {
             Unit<double> rt = Unit<double>::load(P.r_true, u);
             Unit<S> r{cvt<S>(rt.a), cvt<S>(rt.b)};
             r.store(rcur, u);
-            Unit<S> h = Unit<S>::load(hcur, u);
-            rho = rho + cdot(h.a, r.a) + cdot(h.b, r.b);
+            Unit<S> h;
+            if (st.g5) {   // the shadow residual follows: rhat = gamma5 r
+                h = g5u(r, u, N);
+                if (st.m > 0) h.store(hcur, u);
+            } else {
+                h = Unit<S>::load(hcur, u);
+            }
+            if (comp) {
+                if constexpr (sizeof(S) == 4) { cz.add(cdot(h.a, r.a)); cz.add(cdot(h.b, r.b)); }
+            } else {
+                rho = rho + cdot(h.a, r.a) + cdot(h.b, r.b);
+            }
         }
     }
-    cplx<S> v[1] = {rho};
     double2 tot[1];
-    if (reduce_slot<1>(P, CNT_REPLACE, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+    bool last;
+    if (comp) {
+        double2 v[1] = {cz.value()};
+        last = reduce_slot<1>(P, CNT_REPLACE, v, tot, gridDim.x, blockIdx.x);
+    } else {
+        cplx<S> v[1] = {rho};
+        last = reduce_slot<1>(P, CNT_REPLACE, v, tot, gridDim.x, blockIdx.x);
+    }
+    if (last && threadIdx.x == 0) {
         if (run) {
             st.rho_new = tot[0];
             st.rnorm_new = st.true_rnorm;
@@ -766,7 +875,7 @@ __global__ void scalars_kernel(SlotState* states, const SlotPtrs* ptrs) {
     if (threadIdx.x != 0) return;
     SlotState& st = states[blockIdx.x];
     const SlotPtrs& P = ptrs[blockIdx.x];
-    if (!st.live) return;
+    if (!st.live || st.stab) return;
     if (st.status == ST_BREAKDOWN) { st.live = 0; return; }
     const double2 beta = cdiv(st.rho_new, st.rho);
     if (st.m > 0) {
@@ -806,27 +915,198 @@ template <typename S>
 __global__ void __launch_bounds__(BL_THREADS) direction_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
     const SlotState& st = states[blockIdx.y];
     const SlotPtrs& P = ptrs[blockIdx.y];
-    if (st.status != ST_RUNNING) return;
+    if (st.status != ST_RUNNING || st.stab) return;   // BiCGStab slots run their own kernels
     using C = cplx<S>;
     const C be = cvt<S>(st.beta), bec = conj_(be);
     const C al = cvt<S>(st.alpha);
     const bool addx = st.x_dir != 0;
+    const bool g5 = st.g5 != 0;   // gamma5 variant: phat = gamma5 p is never stored
     const void* r = slot_field<S>(P.V, cur_slot(st), N);
     const void* h = slot_field<S>(P.W, cur_slot(st), N);
     const size_t units = N / 2;
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
-        Unit<S> p = Unit<S>::load(P.p, u), ph = Unit<S>::load(P.phat, u);
-        Unit<S> rr = Unit<S>::load(r, u), hh = Unit<S>::load(h, u);
+        Unit<S> p = Unit<S>::load(P.p, u), ph, hh, rr = Unit<S>::load(r, u);
+        if (!g5) { ph = Unit<S>::load(P.phat, u); hh = Unit<S>::load(h, u); }
         if (addx) {   // x_lo += alpha p_{j-1} (owed by the residual update)
             Unit<S> x = Unit<S>::load(P.x_lo, u);
             x.a = x.a + al * p.a; x.b = x.b + al * p.b;
             x.store(P.x_lo, u);
         }
         p.a = rr.a + be * p.a; p.b = rr.b + be * p.b;
-        ph.a = hh.a + bec * ph.a; ph.b = hh.b + bec * ph.b;
         p.store(P.p, u);
-        ph.store(P.phat, u);
+        if (!g5) {
+            ph.a = hh.a + bec * ph.a; ph.b = hh.b + bec * ph.b;
+            ph.store(P.phat, u);
+        }
     }
+}
+
+// ------------------------------------------------------------- BiCGStab
+// The phase-2 solver of Alg. Incremental eigBiCG as the paper runs it (Sec. 2),
+// BiCGStab (van der Vorst) with the shadow start rhat = r_0 (W slot 0):
+//   p = r + beta (p - omega v);  v = A p;  alpha = rho / (rhat, v);  s = r - alpha v;
+//   t = A s;  omega = (t, s) / (t, t);  x += alpha p + omega s;  r = s - omega t;
+//   rho' = (rhat, r);  beta = (rho' / rho) (alpha / omega).
+// Buffers of a slot: r in V slot 0, rhat in W slot 0, p, v = Ap[0], s in the phat
+// buffer, t = Ahp[0]. Two products with A per step, none with A^+.
+
+// p = r + beta (p - omega v); the first step (iter 0) takes p = r.
+template <typename S>
+__global__ void __launch_bounds__(BL_THREADS) stab_dir_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    const SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (st.status != ST_RUNNING || !st.stab) return;
+    using C = cplx<S>;
+    const C be = cvt<S>(st.beta), om = cvt<S>(st.omega);
+    const bool first = st.iter == 0;
+    const size_t units = N / 2;
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+        Unit<S> r = Unit<S>::load(P.V, u);
+        if (!first) {
+            const Unit<S> p = Unit<S>::load(P.p, u), v = Unit<S>::load(P.Ap[0], u);
+            r.a = r.a + be * (p.a - om * v.a);
+            r.b = r.b + be * (p.b - om * v.b);
+        }
+        r.store(P.p, u);
+    }
+}
+
+// PHASE 1: v = A p, sigma = (rhat, v), alpha = rho / sigma.
+// PHASE 2: t = A s, (t, s), (t, t), omega = (t, s) / (t, t).
+// One job per slot (grid: site blocks x slots, slots fastest).
+template <typename S, int THREADS, int MINB, int PHASE>
+__global__ void __launch_bounds__(THREADS, MINB) stab_matvec_kernel(Geom g, const void* links, double kappa,
+                                                                    SlotState* states, const SlotPtrs* ptrs,
+                                                                    int nslots) {
+    const int slot = blockIdx.x % nslots, sblock = blockIdx.x / nslots, nsb = gridDim.x / nslots;
+    SlotState& st = states[slot];
+    const SlotPtrs& P = ptrs[slot];
+    if (st.status != ST_RUNNING || !st.stab) return;
+    using C = cplx<S>;
+    typename LinkSel<S>::type U{reinterpret_cast<decltype(U.u)>(links), g.V};
+    FieldIn<S> in{PHASE == 1 ? P.p : P.phat, g.V};
+    void* out = PHASE == 1 ? P.Ap[0] : P.Ahp[0];
+    const S k = (S)kappa;
+    Acc<S> acc;   // PHASE 1: (rhat, v), |rhat|^2, |v|^2;  PHASE 2: (t, s), (t, t), |s|^2
+    for (int s = sblock * blockDim.x + threadIdx.x; s < g.V; s += nsb * blockDim.x) {
+        C o[12], self[12];
+        hop_site<false, S>(g, U, in, s, o);
+        in.load(s, self);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) o[c] = self[c] - k * o[c];
+        Field<S>::store(out, g.V, s, o);
+        if (PHASE == 1) {
+            C h[12];
+            Field<S>::load(P.W, g.V, s, h);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                acc.z = acc.z + cdot(h[c], o[c]);
+                acc.a += abs2(h[c]);
+                acc.b += abs2(o[c]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                acc.z = acc.z + cdot(o[c], self[c]);
+                acc.a += abs2(o[c]);
+                acc.b += abs2(self[c]);
+            }
+        }
+    }
+    cplx<S> v[2];
+    acc.to(v);
+    double2 tot[2];
+    if (reduce_slot<2>(P, CNT_MATVEC, v, tot, nsb, sblock) && threadIdx.x == 0) {
+        st.matvecs += 1;
+        if (PHASE == 1) {
+            st.sigma = tot[0];
+            st.phat_norm = sqrt(tot[1].x);
+            st.ap_norm = sqrt(tot[1].y);
+            if (!(cabs_(st.sigma) >= BREAK_TOL * st.phat_norm * st.ap_norm) || cabs2(st.sigma) == 0.0)
+                st.status = ST_BREAKDOWN;
+            else
+                st.alpha = cdiv(st.rho, st.sigma);
+        } else {
+            st.ts = tot[0];
+            st.tt = tot[1].x;
+            st.omega = st.tt > 0.0 ? cdiv(st.ts, make_double2(st.tt, 0.0)) : make_double2(0.0, 0.0);
+        }
+    }
+}
+
+// s = r - alpha v  (into the phat buffer)
+template <typename S>
+__global__ void __launch_bounds__(BL_THREADS) stab_s_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    const SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (st.status != ST_RUNNING || !st.stab) return;
+    const cplx<S> al = cvt<S>(st.alpha);
+    const size_t units = N / 2;
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+        Unit<S> r = Unit<S>::load(P.V, u);
+        const Unit<S> v = Unit<S>::load(P.Ap[0], u);
+        r.a = r.a - al * v.a;
+        r.b = r.b - al * v.b;
+        r.store(P.phat, u);
+    }
+}
+
+// x_lo += alpha p + omega s;  r = s - omega t;  rho' = (rhat, r), ||r||; the
+// reliable-update flags as in the BiCG residual update.
+template <typename S>
+__global__ void __launch_bounds__(BL_THREADS) stab_update_kernel(SlotState* states, const SlotPtrs* ptrs, size_t N) {
+    SlotState& st = states[blockIdx.y];
+    const SlotPtrs& P = ptrs[blockIdx.y];
+    if (st.status != ST_RUNNING || !st.stab) return;
+    using C = cplx<S>;
+    const C al = cvt<S>(st.alpha), om = cvt<S>(st.omega);
+    Acc<S> acc;   // rho', |r|^2
+    const size_t units = N / 2;
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+        Unit<S> x = Unit<S>::load(P.x_lo, u);
+        const Unit<S> p = Unit<S>::load(P.p, u), sv = Unit<S>::load(P.phat, u), t = Unit<S>::load(P.Ahp[0], u);
+        const Unit<S> h = Unit<S>::load(P.W, u);
+        x.a = x.a + al * p.a + om * sv.a;
+        x.b = x.b + al * p.b + om * sv.b;
+        x.store(P.x_lo, u);
+        Unit<S> r{sv.a - om * t.a, sv.b - om * t.b};
+        r.store(P.V, u);
+        acc.z = acc.z + cdot(h.a, r.a) + cdot(h.b, r.b);
+        acc.a += abs2(r.a) + abs2(r.b);
+    }
+    cplx<S> v[2];
+    acc.to(v);
+    double2 tot[2];
+    if (reduce_slot<2>(P, CNT_UPDATE, v, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
+        st.rho_new = tot[0];
+        st.rnorm_new = sqrt(tot[1].x);
+        st.x_owed = 0;   // x is complete after this step
+        if (!isfinite(st.rnorm_new) || !isfinite(st.rho_new.x) || !isfinite(st.rho_new.y)) {
+            st.status = ST_BREAKDOWN;
+        } else {
+            if (st.rnorm_new <= st.tol * st.bnorm) st.need_ru = 1;
+            if (st.rnorm_new > st.rmax) st.rmax = st.rnorm_new;
+            if (st.delta > 0.0 && (st.rnorm_new < st.delta * st.r_ru || st.rnorm_new < 1e-3 * st.rmax)) st.need_ru = 1;
+        }
+    }
+}
+
+// beta = (rho' / rho) (alpha / omega); counters; maxiter and breakdown (rho or omega).
+__global__ void stab_scalars_kernel(SlotState* states) {
+    if (threadIdx.x != 0) return;
+    SlotState& st = states[blockIdx.x];
+    if (!st.live || !st.stab) return;
+    if (st.status == ST_BREAKDOWN) { st.live = 0; return; }
+    st.iter += 1;
+    const bool om0 = cabs2(st.omega) == 0.0;
+    if (!om0) st.beta = cdiv(st.rho_new, st.rho) * cdiv(st.alpha, st.omega);
+    st.rho = st.rho_new;
+    st.rnorm = st.rnorm_new;
+    if (st.status == ST_RUNNING) {
+        if (st.iter >= st.maxiter) st.status = ST_NOCONV;
+        else if (om0 || !(cabs_(st.rho) >= BREAK_TOL * st.rhat_norm * st.rnorm)) st.status = ST_BREAKDOWN;
+    }
+    if (st.status != ST_RUNNING) st.live = 0;
 }
 
 // Fold x_lo into x_hi at the end of a solve (x = 0 for a zero source).
@@ -1105,7 +1385,7 @@ cudaError_t launch_multidot(int a, const void* X, int xp, int b, const void* Y, 
 }
 
 cudaError_t launch_vupdate(int a, const void* X, int xp, const double2* D, int ldd, int b, void* Y, int yp,
-                           int overwrite, size_t N, cudaStream_t st) {
+                           int overwrite, size_t N, cudaStream_t st, int fp64_arith) {
     if (a > MAX_SMALL) return cudaErrorInvalidValue;
     for (int j0 = 0; j0 < b; j0 += MD_BMAX) {
         const int bb = b - j0 < MD_BMAX ? b - j0 : MD_BMAX;
@@ -1113,6 +1393,7 @@ cudaError_t launch_vupdate(int a, const void* X, int xp, const double2* D, int l
         const double2* Dj = D + j0;
         int nb = blas_blocks(N);
         if (xp == 1 && yp == 1) vupdate_kernel<float, float, float><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
+        else if (xp == 1 && yp == 0 && fp64_arith) vupdate_kernel<float, double, double><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
         else if (xp == 1 && yp == 0) vupdate_kernel<float, double, float><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
         else if (xp == 0 && yp == 1) vupdate_kernel<double, float, double><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
         else vupdate_kernel<double, double, double><<<nb, BL_THREADS, 0, st>>>(a, X, Dj, ldd, bb, Yj, overwrite, N);
@@ -1163,13 +1444,14 @@ cudaError_t launch_bicg_start(const Geom& g, const void* links64, double kappa, 
 
 // SPT: sites per thread (grid-stride), which amortises each block's set-up and
 // reduction tail over more sites.
-template <typename S, int THREADS, int MINB, bool PAIR, int BZ = 0, int SPT = 1>
+template <typename S, int THREADS, int MINB, bool PAIR, int BZ = 0, int SPT = 1, bool G5 = false>
 static void matvec_launch(const Geom& g, const void* links, double kappa, SlotState* states, const SlotPtrs* ptrs,
                           int nslots, cudaStream_t s) {
-    const int njobs = PAIR ? nslots : 2 * nslots;
+    const int njobs = (PAIR || G5) ? nslots : 2 * nslots;
     int nb = div_up((size_t)g.V, (size_t)THREADS * SPT);
     if (nb > PARTIAL_STRIDE / 2) nb = PARTIAL_STRIDE / 2;
-    matvec_kernel<S, THREADS, MINB, PAIR, BZ><<<nb * njobs, THREADS, 0, s>>>(g, links, kappa, states, ptrs, njobs);
+    matvec_kernel<S, THREADS, MINB, PAIR, BZ, G5><<<nb * njobs, THREADS, 0, s>>>(g, links, kappa, states, ptrs,
+                                                                                njobs);
 }
 // The brick shapes need Lx, Ly multiples of 8 and Lz a multiple of BZ.
 static bool brick_ok(const Geom& g, int bz) { return g.L[0] % 8 == 0 && g.L[1] % 8 == 0 && g.L[2] % bz == 0; }
@@ -1214,6 +1496,36 @@ cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, i
             case 17: matvec_launch<float, 128, 4, true, 0, 4>(g, links, kappa, states, ptrs, nslots, s); break;
             case 18: matvec_launch<float, 256, 2, true, 0, 2>(g, links, kappa, states, ptrs, nslots, s); break;
             default: matvec_launch<float, 128, 1, false>(g, links, kappa, states, ptrs, nslots, s); break;
+        }
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// The gamma5 variant's operator (A p only, sigma with phat = gamma5 p): the
+// one-operator shapes of the list above (per-site threads, no operator pairing).
+bool matvec_g5_variant_ok(const Geom& g, int v) {
+    switch (v) {
+        case 0: case 1: case 2: case 5: case 6: case 9: case 16: return true;
+        case 13: return brick_ok(g, 4);
+        default: return false;
+    }
+}
+
+cudaError_t launch_bicg_matvec_g5(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
+                                  const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant) {
+    if (prec == 0) {
+        matvec_launch<double, 128, 1, false, 0, 1, true>(g, links, kappa, states, ptrs, nslots, s);
+    } else {
+        switch (variant) {
+            case 1: matvec_launch<float, 128, 6, false, 0, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 2: matvec_launch<float, 256, 3, false, 0, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 5: matvec_launch<float, 128, 4, false, 0, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 6: matvec_launch<float, 128, 5, false, 0, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 9: matvec_launch<float, 64, 8, false, 0, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 13: matvec_launch<float, 256, 3, false, 4, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 16: matvec_launch<float, 256, 3, false, 0, 4, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            default: matvec_launch<float, 128, 1, false, 0, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
         }
     }
     count_launches(1);
@@ -1272,6 +1584,40 @@ cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int
     if (e != cudaSuccess) return e;
     if (prec == 0) replace_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     else replace_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename S, int THREADS, int MINB, int PHASE>
+static void stab_matvec_launch(const Geom& g, const void* links, double kappa, SlotState* states,
+                               const SlotPtrs* ptrs, int nslots, cudaStream_t s) {
+    int nb = div_up((size_t)g.V, (size_t)THREADS * 2);
+    if (nb > PARTIAL_STRIDE / 2) nb = PARTIAL_STRIDE / 2;
+    stab_matvec_kernel<S, THREADS, MINB, PHASE><<<nb * nslots, THREADS, 0, s>>>(g, links, kappa, states, ptrs, nslots);
+}
+
+cudaError_t launch_stab_step(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
+                             const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s) {
+    dim3 grid(blas_blocks(N / 2), nslots);
+    if (prec == 0) {
+        stab_dir_kernel<double><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+        stab_matvec_launch<double, 128, 1, 1>(g, links, kappa, states, ptrs, nslots, s);
+        stab_s_kernel<double><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+        stab_matvec_launch<double, 128, 1, 2>(g, links, kappa, states, ptrs, nslots, s);
+        stab_update_kernel<double><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    } else {
+        stab_dir_kernel<float><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+        stab_matvec_launch<float, 128, 4, 1>(g, links, kappa, states, ptrs, nslots, s);
+        stab_s_kernel<float><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+        stab_matvec_launch<float, 128, 4, 2>(g, links, kappa, states, ptrs, nslots, s);
+        stab_update_kernel<float><<<grid, BL_THREADS, 0, s>>>(states, ptrs, N);
+    }
+    count_launches(5);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stab_scalars(SlotState* states, int nslots, cudaStream_t s) {
+    stab_scalars_kernel<<<nslots, 32, 0, s>>>(states);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -61,9 +61,11 @@ cudaError_t launch_dots_tc(int a, const void* X, size_t x_stride, int b, const v
                            double2* C, int ldc, int conj_store, double* scratch, size_t scratch_doubles, int* err,
                            cudaStream_t st);
 // overwrite = 0: Y_j += sum_i X_i D[i*ldd + j];  overwrite = 1: Y_j = sum_i X_i D[i*ldd + j].
-// The arithmetic is FP32 when X is FP32 (the sum is added to an FP64 Y in FP64).
+// The arithmetic is FP32 when X is FP32 (the sum is added to an FP64 Y in FP64),
+// unless fp64_arith is set and Y is FP64 (coefficients with large, cancelling
+// entries, e.g. eigenvectors in a nearly dependent basis).
 cudaError_t launch_vupdate(int a, const void* X, int xprec, const double2* D, int ldd, int b,
-                           void* Y, int yprec, int overwrite, size_t N, cudaStream_t st);
+                           void* Y, int yprec, int overwrite, size_t N, cudaStream_t st, int fp64_arith = 0);
 // out[j] = ||Y_j|| (FP64 result, device) for b fields.
 cudaError_t launch_norms(int b, const void* Y, int yprec, size_t N, double* out, double2* scratch,
                          size_t scratch_elems, cudaStream_t st);
@@ -92,6 +94,10 @@ int matvec_variants();
 bool matvec_variant_ok(const Geom& g, int v);
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec,
                                SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant);
+// gamma5 variant (Sec. 4): A p only, phat = gamma5 p; shapes v with matvec_g5_variant_ok.
+bool matvec_g5_variant_ok(const Geom& g, int v);
+cudaError_t launch_bicg_matvec_g5(const Geom& g, const void* links, double kappa, int prec,
+                                  SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant);
 cudaError_t launch_bicg_update(int prec, SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
 // ru_variant: true-residual kernel shape (0 .. true_resid_variants()-1, timed at init);
 // RU_DF and RU_DF + 1 evaluate A x_hi in double-float arithmetic (needs links_df
@@ -104,6 +110,12 @@ cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int
 // FP64 links -> double-float links (n complex elements).
 cudaError_t launch_links_df(const double2* l64, float4* ldf, size_t n, cudaStream_t st);
 cudaError_t launch_bicg_scalars(SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s);
+// BiCGStab step over the slots with stab set (direction, v = A p with alpha, s,
+// t = A s with omega, x and r update with rho and the reliable-update flags),
+// then (after launch_bicg_ru) the scalars: beta, counters, maxiter, breakdown.
+cudaError_t launch_stab_step(const Geom& g, const void* links, double kappa, int prec, SlotState* st_,
+                             const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
+cudaError_t launch_stab_scalars(SlotState* st_, int nslots, cudaStream_t s);
 cudaError_t launch_bicg_direction(int prec, SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
 cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa, int prec,
                                SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s,
@@ -131,6 +143,16 @@ cudaError_t launch_lu_factor(int n, double2* A, int lda, int* piv, int* info, cu
 // Solve A X = B (trans = 0) or A^H X = B (trans = 1) with the LU factors; B is n x nrhs (ldb), in place.
 cudaError_t launch_lu_solve(int n, const double2* LU, int lda, const int* piv, int trans, int nrhs,
                             double2* B, int ldb, cudaStream_t st);
+// One factor of P A = L U (from launch_lu_factor) applied to B:
+// LU_LEFT_PL: B <- L^{-1} P B; LU_LEFT_U: B <- U^{-1} B (n x ncols);
+// LU_RIGHT_U: B <- B U^{-1} (ncols rows of n); LU_LEFT_LH: B <- P^T L^{-H} B.
+enum LuPart { LU_LEFT_PL = 0, LU_LEFT_U = 1, LU_RIGHT_U = 2, LU_LEFT_LH = 3 };
+cudaError_t launch_lu_part(int n, const double2* LU, int lda, const int* piv, int part, int ncols, double2* B,
+                           int ldb, cudaStream_t st);
+// Rank-revealing selection of a small square block B (n <= 32): complete-pivoting
+// LU stopped at the first pivot below tau * |first pivot|; out[0] = pivots kept r,
+// out[1 + i], out[1 + n + i] = row and column index of pivot i.
+cudaError_t launch_pivot_select(int n, const double2* B, int ld, double tau, int* out, cudaStream_t st);
 // Final Ritz pairs of one slot's window: eig(H^(vs)), nev smallest;
 // coefficients Y (vs x nev) and Z into Yc/Zc with the window scales folded in.
 cudaError_t launch_final_ritz(SlotState* st_, const SlotPtrs* ptrs, int slot, double2* Yc, double2* Zc,

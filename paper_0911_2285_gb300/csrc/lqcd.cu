@@ -58,6 +58,9 @@ struct lqcd_ctx {
     size_t kbytes = 0;       // bytes per Krylov field
     size_t dbytes = 0;       // bytes per FP64 field
     int kmax = 1, m = 0, nev = 0, n_def_max = 0, nslot_win = 0;
+    int kbatch = 1;                 // right-hand sides per batched launch (<= kmax; autotuned for k_max = 0)
+    bool k_auto = false;
+    double k_ms[MAX_SLOTS + 1] = {};   // autotuner: ms of one iteration (operator, updates) per batch size
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<void*> allocs;
@@ -76,7 +79,16 @@ struct lqcd_ctx {
     double2* x_hi_all = nullptr;    // kmax FP64 fields
     double2* b_all = nullptr;
     double2* rt_all = nullptr;
-    char* win_all = nullptr;        // kmax * 2 * (m+1) Krylov fields
+    char* vw_base = nullptr;        // 2 kmax Krylov fields: [V_0 .. V_{K-1}][W_0 .. W_{K-1}], the
+                                    // residual and shadow residual of a slot without a window
+    // eigBiCG windows (2 (m+1) Krylov fields each), attached to a slot while it
+    // runs windowed: allocated from the context's stream-ordered pool when the
+    // memory plan has room (hbm_budget_bytes, or free device memory), freed after
+    cudaMemPool_t win_pool = nullptr;
+    void* win[MAX_SLOTS] = {};
+    size_t win_bytes = 0;           // bytes of one window
+    size_t plan_bytes = 0;          // memory plan of everything else (fixed at init)
+    int win_attached = 0;
     char* vec_all = nullptr;        // kmax * 6 Krylov fields (p, phat, Ap[2], Ahp[2])
     double2* small_all = nullptr;   // per-slot small matrices
     size_t small_stride = 0;
@@ -111,9 +123,9 @@ struct lqcd_ctx {
     int* d_err = nullptr;           // device error word of the bounded waits
     std::vector<double> tune_ms;    // autotuner timings per variant
 
-    // CUDA graphs of CHECK_EVERY iterations, keyed by (nslots, windowed)
-    cudaGraphExec_t graphs[MAX_SLOTS + 1][2] = {};
-    long long graph_nodes[MAX_SLOTS + 1][2] = {};
+    // CUDA graphs of CHECK_EVERY iterations, keyed by (nslots, kernel groups CH_*)
+    cudaGraphExec_t graphs[MAX_SLOTS + 1][8] = {};
+    long long graph_nodes[MAX_SLOTS + 1][8] = {};
 
     // serving session (lqcd_submit / lqcd_progress / lqcd_poll): requests wait in
     // a queue, take a batch slot as soon as one is free, and leave it when done
@@ -130,7 +142,8 @@ struct lqcd_ctx {
         lqcd_mode md = LQCD_MODE_PLAIN;
         bool windowed = false;
         bool deftol_pending = false;   // first leg of the DefTol restart still running
-        int first_iters = 0, first_matvecs = 0, first_ru = 0, outer = 0;
+        bool correction_pending = false;   // mixed eigBiCG: the window leg is still running
+        int first_iters = 0, first_matvecs = 0, first_ru = 0, first_restarts = 0, outer = 0;
         std::chrono::steady_clock::time_point t0;
     };
     struct Finished {
@@ -193,6 +206,9 @@ lqcd_status validate(const lqcd_params* p) {
     if (p->k_max < 0 || p->k_max > MAX_SLOTS) return LQCD_ERR_ARG;
     if (p->n_def_max < 0 || p->n_def_max > MAX_SMALL) return LQCD_ERR_ARG;
     if (p->n1 < 0 || p->deftol < 0.0 || p->delta < 0.0 || p->delta >= 1.0) return LQCD_ERR_ARG;
+    if (p->gamma5 != 0 && p->gamma5 != 1) return LQCD_ERR_ARG;
+    if (p->bicgstab != 0 && p->bicgstab != 1) return LQCD_ERR_ARG;
+    if (p->bicgstab && p->gamma5) return LQCD_ERR_ARG;   // the gamma5 variant is a BiCG recursion
     return LQCD_OK;
 }
 
@@ -205,9 +221,9 @@ lqcd_status set_ptrs(lqcd_ctx* c) {
         P.b = c->b_all + (size_t)s * c->N;
         P.r_true = c->rt_all + (size_t)s * c->N;
         P.x_df = c->xdf_all ? c->xdf_all + (size_t)s * c->N : nullptr;
-        const size_t wslots = (size_t)(c->m + 1);
-        P.V = c->krylov(c->win_all, (size_t)s * 2 * wslots);
-        P.W = c->krylov(c->win_all, (size_t)s * 2 * wslots + wslots);
+        P.V = c->win[s] ? c->win[s] : c->krylov(c->vw_base, s);
+        P.W = c->win[s] ? reinterpret_cast<char*>(c->win[s]) + (size_t)(c->m + 1) * c->kbytes
+                        : c->krylov(c->vw_base, (size_t)c->kmax + s);
         char* vb = c->vec_all + (size_t)s * 6 * c->kbytes;
         P.p = vb;
         P.phat = vb + c->kbytes;
@@ -227,6 +243,56 @@ lqcd_status set_ptrs(lqcd_ctx* c) {
         P.counters = c->counters + (size_t)s * CNT_COUNT;
     }
     CK(cudaMemcpy(c->d_ptrs, c->h_ptrs.data(), sizeof(SlotPtrs) * c->kmax, cudaMemcpyHostToDevice));
+    return LQCD_OK;
+}
+
+// Point slot s's V and W at its window (attached) or at its base fields.
+lqcd_status upload_ptrs(lqcd_ctx* c, int s) {
+    SlotPtrs& P = c->h_ptrs[s];
+    P.V = c->win[s] ? c->win[s] : c->krylov(c->vw_base, s);
+    P.W = c->win[s] ? reinterpret_cast<char*>(c->win[s]) + (size_t)(c->m + 1) * c->kbytes
+                    : c->krylov(c->vw_base, (size_t)c->kmax + s);
+    CK(cudaMemcpyAsync(c->d_ptrs + s, &P, sizeof(SlotPtrs), cudaMemcpyHostToDevice, c->stream));
+    return LQCD_OK;
+}
+
+constexpr size_t WIN_RESERVE = (size_t)1 << 30;   // device memory left free when there is no budget
+
+// Admission by device memory: give slot s an eigBiCG window if the memory plan has
+// room for one more (hbm_budget_bytes, else the free device memory less a reserve).
+// *ok = false (and LQCD_OK) when it does not fit now.
+lqcd_status attach_window(lqcd_ctx* c, int s, bool* ok) {
+    *ok = false;
+    if (c->win[s]) { *ok = true; return LQCD_OK; }
+    if (c->p.hbm_budget_bytes) {
+        if (c->plan_bytes + (size_t)(c->win_attached + 1) * c->win_bytes > c->p.hbm_budget_bytes) return LQCD_OK;
+    } else {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        if (fr < c->win_bytes + WIN_RESERVE) return LQCD_OK;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, c->win_bytes, c->win_pool, c->stream);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        return LQCD_OK;
+    }
+    CK(e);
+    CK(cudaMemsetAsync(p, 0, c->win_bytes, c->stream));
+    c->win[s] = p;
+    c->win_attached += 1;
+    *ok = true;
+    return upload_ptrs(c, s);
+}
+
+lqcd_status detach_window(lqcd_ctx* c, int s) {
+    if (!c->win[s]) return LQCD_OK;
+    void* p = c->win[s];
+    c->win[s] = nullptr;
+    c->win_attached -= 1;
+    lqcd_status r = upload_ptrs(c, s);
+    if (r != LQCD_OK) return r;
+    CK(cudaFreeAsync(p, c->stream));
     return LQCD_OK;
 }
 
@@ -265,6 +331,7 @@ __global__ void inv_norm_kernel(const double2* G, int ld, int n, double2* sc, do
 }  // namespace
 
 static lqcd_status autotune(lqcd_ctx* c);
+static lqcd_status autotune_batch(lqcd_ctx* c);
 
 // ============================================================== lifecycle
 extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* params, const double* links,
@@ -275,6 +342,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     if (vs != LQCD_OK) return vs;
     lqcd_ctx* c = new lqcd_ctx();
     c->p = *params;
+    c->k_auto = params->k_max == 0;
     if (const char* f = getenv("LQCD_FAULT")) {
         int n = 0;
         if (sscanf(f, "alloc:%d", &n) == 1 && n > 0) c->fault_alloc = n;
@@ -300,9 +368,11 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     // Memory plan (bytes) for the HBM budget check.
     const size_t K = (size_t)c->kmax;
     size_t plan = (size_t)c->V * 4 * 9 * 16 + (c->kprec ? (size_t)c->V * 4 * (3 + 9) * 16 + K * c->N * 16 : 0);
-    plan += K * c->kbytes * (1 + 2 * (c->m + 1) + 6) + K * c->dbytes * 4;
+    plan += K * c->kbytes * (1 + 2 + 6) + K * c->dbytes * 4;
     plan += 2 * (size_t)c->n_def_max * c->kbytes;
     plan += (MAX_SLOTS * eig_work_elems() + 16) * 16 + c->mdscratch_elems * 16 + K * CNT_COUNT * PARTIAL_STRIDE * 16;
+    c->plan_bytes = plan;
+    c->win_bytes = (size_t)2 * (c->m + 1) * c->kbytes;
     if (c->p.hbm_budget_bytes && plan > c->p.hbm_budget_bytes) {
         g_last_error = "memory plan exceeds hbm_budget_bytes";
         delete c;
@@ -336,7 +406,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     AL(c->x_hi_all, K * c->dbytes);
     AL(c->b_all, K * c->dbytes);
     AL(c->rt_all, K * c->dbytes);
-    AL(c->win_all, K * 2 * (c->m + 1) * c->kbytes);
+    AL(c->vw_base, K * 2 * c->kbytes);
     AL(c->vec_all, K * 6 * c->kbytes);
     AL(c->small_all, K * c->small_stride * 16);
     AL(c->partials, K * CNT_COUNT * PARTIAL_STRIDE * 16);
@@ -361,7 +431,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
 #undef AL
     if ((e = cudaMemset(c->counters, 0, K * CNT_COUNT * sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemset(c->small_all, 0, K * c->small_stride * 16)) != cudaSuccess ||
-        (e = cudaMemset(c->win_all, 0, K * 2 * (c->m + 1) * c->kbytes)) != cudaSuccess ||
+        (e = cudaMemset(c->vw_base, 0, K * 2 * c->kbytes)) != cudaSuccess ||
         (e = cudaMemset(c->vec_all, 0, K * 6 * c->kbytes)) != cudaSuccess ||
         (e = cudaMemset(c->x_lo_all, 0, K * c->kbytes)) != cudaSuccess ||
         (e = cudaMemset(c->d_err, 0, 16)) != cudaSuccess) {
@@ -375,6 +445,18 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     if ((e = cudaMemcpy(c->d_state, c->h_state, sizeof(SlotState) * K, cudaMemcpyHostToDevice)) != cudaSuccess) {
         set_error("cudaMemcpy state", e);
         return fail(LQCD_ERR_CUDA);
+    }
+    {
+        int dev = 0;
+        cudaMemPoolProps pp;
+        memset(&pp, 0, sizeof(pp));
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.location.type = cudaMemLocationTypeDevice;
+        if ((e = cudaGetDevice(&dev)) == cudaSuccess) {
+            pp.location.id = dev;
+            e = cudaMemPoolCreate(&c->win_pool, &pp);
+        }
+        if (e != cudaSuccess) { set_error("cudaMemPoolCreate", e); c->win_pool = nullptr; return fail(LQCD_ERR_CUDA); }
     }
     lqcd_status st = set_ptrs(c);
     if (st != LQCD_OK) return fail(st);
@@ -396,9 +478,14 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     c->last_restarts.assign(c->kmax, 0);
     if ((e = prepare_eig_kernels()) != cudaSuccess) { set_error("prepare_eig_kernels", e); return fail(LQCD_ERR_CUDA); }
     if ((e = prepare_tiled_kernel()) != cudaSuccess) { set_error("prepare_tiled_kernel", e); return fail(LQCD_ERR_CUDA); }
-    for (int n = 1; n <= c->kmax; ++n) c->tile_ok[n] = c->kprec && tiled_plan(c->g, n, &c->tgeo[n]);
+    for (int n = 1; n <= c->kmax; ++n) c->tile_ok[n] = c->kprec && !c->p.gamma5 && tiled_plan(c->g, n, &c->tgeo[n]);
     st = autotune(c);
     if (st != LQCD_OK) return fail(st);
+    c->kbatch = c->kmax;
+    if (c->k_auto) {
+        st = autotune_batch(c);
+        if (st != LQCD_OK) return fail(st);
+    }
     *out = c;
     return LQCD_OK;
 }
@@ -407,8 +494,12 @@ extern "C" void lqcd_destroy(lqcd_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (int i = 0; i <= MAX_SLOTS; ++i)
-        for (int j = 0; j < 2; ++j)
+        for (int j = 0; j < 8; ++j)
             if (c->graphs[i][j]) cudaGraphExecDestroy(c->graphs[i][j]);
+    for (int s = 0; s < MAX_SLOTS; ++s)
+        if (c->win[s]) cudaFreeAsync(c->win[s], c->stream);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->win_pool) cudaMemPoolDestroy(c->win_pool);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->chunk_ev) cudaEventDestroy(c->chunk_ev);
@@ -492,9 +583,12 @@ lqcd_status apply_fields(lqcd_ctx* c, int prec, int dagger, int nf, const void* 
 }
 
 // r = b - A x for nf FP64 fields (consecutive slots): FP32 hop arithmetic in
-// mixed precision (the result feeds FP32 work), FP64 otherwise.
-lqcd_status residual_fields(lqcd_ctx* c, int nf, const double2* x, double2* r, const double2* b) {
-    if (!c->kprec) return apply_fields(c, 0, 0, nf, x, c->dbytes, r, c->dbytes, b);
+// mixed precision (the result feeds FP32 work), FP64 otherwise or when precise
+// is set (a residual far below ||A|| ||x||, e.g. after a first solve leg, where
+// FP32 hop rounding would swamp it).
+lqcd_status residual_fields(lqcd_ctx* c, int nf, const double2* x, double2* r, const double2* b,
+                            bool precise = false) {
+    if (!c->kprec || precise) return apply_fields(c, 0, 0, nf, x, c->dbytes, r, c->dbytes, b);
     std::vector<ApplyJob> jobs(2 * c->kmax);
     for (int j0 = 0; j0 < nf; j0 += 2 * c->kmax) {
         const int nb = std::min(2 * c->kmax, nf - j0);
@@ -522,7 +616,7 @@ extern "C" lqcd_status lqcd_apply(lqcd_ctx* c, int dagger, lqcd_precision prec, 
     for (int j0 = 0; j0 < k; j0 += c->kmax) {
         const int kb = std::min(c->kmax, k - j0);
         void* fin = pr ? (void*)c->x_lo_all : (void*)c->x_hi_all;
-        void* fout = pr ? (void*)c->win_all : (void*)c->rt_all;
+        void* fout = pr ? (void*)c->vw_base : (void*)c->rt_all;
         const size_t fb = c->N * (pr ? 8 : 16);
         lqcd_status s = upload(c, in + (size_t)j0 * 2 * c->N, kb, fin, pr, on_device);
         if (s != LQCD_OK) return s;
@@ -538,13 +632,14 @@ extern "C" lqcd_status lqcd_apply(lqcd_ctx* c, int dagger, lqcd_precision prec, 
 // ============================================================ deflation
 namespace {
 
-// x_hi[j] += U_r H^{-1} U_l^H (b_j - A x_hi[j]) for slots s0 .. s0+k-1.
-lqcd_status deflate_range(lqcd_ctx* c, int s0, int k) {
+// x_hi[j] += U_r H^{-1} U_l^H (b_j - A x_hi[j]) for slots s0 .. s0+k-1
+// (precise: FP64 residual, see residual_fields).
+lqcd_status deflate_range(lqcd_ctx* c, int s0, int k, bool precise = false) {
     const int n = c->n_def;
     if (n == 0 || k == 0) return LQCD_OK;
     double2* xh = c->x_hi_all + (size_t)s0 * c->N;
     double2* rt = c->rt_all + (size_t)s0 * c->N;
-    lqcd_status s = residual_fields(c, k, xh, rt, c->b_all + (size_t)s0 * c->N);
+    lqcd_status s = residual_fields(c, k, xh, rt, c->b_all + (size_t)s0 * c->N, precise);
     if (s != LQCD_OK) return s;
     double2* C = c->dsmall;   // n x k, ld k
     const void* R = rt;
@@ -560,7 +655,7 @@ lqcd_status deflate_range(lqcd_ctx* c, int s0, int k) {
     CK(launch_vupdate(n, c->Ur, c->kprec, C, k, k, xh, 0, 0, c->N, c->stream));
     return LQCD_OK;
 }
-lqcd_status deflate_slots(lqcd_ctx* c, int k) { return deflate_range(c, 0, k); }
+lqcd_status deflate_slots(lqcd_ctx* c, int k, bool precise = false) { return deflate_range(c, 0, k, precise); }
 
 lqcd_status refactor(lqcd_ctx* c) {
     const int n = c->n_def, ld = c->n_def_max;
@@ -612,12 +707,16 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, void* work) {
     std::vector<double> hn(4 * nn);
     CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * 4 * nn, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    // keep pairs whose projected columns retain more than 1e-8 of their norm
+    // keep pairs whose projected columns retain more than drop of their norm:
+    // 1e-8 with FP64 vectors; with FP32 vectors the projection itself carries
+    // errors of order 1e-6 of the column, so a column that keeps less than 1e-3
+    // is mostly rounding noise and would only make the bases nearly dependent
+    const double drop = c->kprec ? 1e-3 : 1e-8;
     std::vector<int> keep;
     std::vector<double2> hsc(2 * nn, make_double2(0.0, 0.0));
     for (int i = 0; i < nn; ++i) {
         const double nv0 = hn[i], nw0 = hn[nn + i], nv = hn[2 * nn + i], nw = hn[3 * nn + i];
-        if (nv > 1e-8 * nv0 && nw > 1e-8 * nw0 && std::isfinite(nv) && std::isfinite(nw)) keep.push_back(i);
+        if (nv > drop * nv0 && nw > drop * nw0 && std::isfinite(nv) && std::isfinite(nw)) keep.push_back(i);
         hsc[i] = make_double2(nv > 0 ? 1.0 / nv : 0.0, 0.0);
         hsc[nn + i] = make_double2(nw > 0 ? 1.0 / nw : 0.0, 0.0);
     }
@@ -634,6 +733,38 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, void* work) {
         ++kk;
     }
     if (kk == 0) return LQCD_OK;
+    if (kp && kk > 1) {
+        // FP32 vectors: the Ritz pairs of one window can be nearly dependent among
+        // themselves (repeated copies of a converged pair in a finite-precision
+        // Lanczos run), which the column norms above do not see. A complete-pivoting
+        // LU of the block W'^H V' keeps a well-conditioned subset: columns of V' and
+        // W' of the pivots down to 1e-3 of the first.
+        double2* Mb = T1;
+        int* sel = reinterpret_cast<int*>(nrm + 4 * nn + 8);
+        CK(launch_multidot(kk, Wn, kp, kk, Vn, kp, c->N, Mb, kk, 0, c->mdscratch, c->mdscratch_elems, c->stream,
+                           c->d_err, c->use_tc));
+        CK(launch_pivot_select(kk, Mb, kk, 1e-3, sel, c->stream));
+        std::vector<int> hsel(1 + 2 * kk);
+        CK(cudaMemcpyAsync(hsel.data(), sel, sizeof(int) * (1 + 2 * kk), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const int r = std::max(0, std::min(hsel[0], kk));
+        if (r < kk) {
+            std::vector<int> wi(hsel.begin() + 1, hsel.begin() + 1 + r);
+            std::vector<int> vi(hsel.begin() + 1 + kk, hsel.begin() + 1 + kk + r);
+            std::sort(wi.begin(), wi.end());
+            std::sort(vi.begin(), vi.end());
+            for (int t = 0; t < r; ++t) {   // ascending subsets: each copy moves a column down
+                if (vi[t] != t)
+                    CK(cudaMemcpyAsync(c->krylov(c->Ur, n + t), c->krylov(c->Ur, n + vi[t]), c->kbytes,
+                                       cudaMemcpyDeviceToDevice, c->stream));
+                if (wi[t] != t)
+                    CK(cudaMemcpyAsync(c->krylov(c->Ul, n + t), c->krylov(c->Ul, n + wi[t]), c->kbytes,
+                                       cudaMemcpyDeviceToDevice, c->stream));
+            }
+            kk = r;
+        }
+        if (kk == 0) return LQCD_OK;
+    }
     // [A V' | V'] and [A^H W' | W'] side by side in the work area, in the storage
     // precision (FP32 operator with two-row links for FP32 storage: the
     // projections are FP32 sums as well, and lqcd_eigs recomputes its pencil in FP64)
@@ -689,6 +820,11 @@ namespace {
 
 // The operator pair of one iteration in the autotuned kernel shape.
 cudaError_t launch_matvec(lqcd_ctx* c, int nslots, int variant) {
+    if (c->p.gamma5) {
+        const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
+        return launch_bicg_matvec_g5(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->stream,
+                                     variant);
+    }
     if (variant == TILED && c->tile_ok[nslots])
         return launch_matvec_tiled(c->g, c->tgeo[nslots], c->links32, c->p.kappa, c->d_state, c->d_ptrs, c->d_err,
                                    c->stream);
@@ -698,65 +834,86 @@ cudaError_t launch_matvec(lqcd_ctx* c, int nslots, int variant) {
 }
 
 // One chunk of CHECK_EVERY iterations for nslots slots (graph body).
-lqcd_status enqueue_chunk(lqcd_ctx* c, int nslots, int windowed) {
+// Kernel groups of an iteration chunk (bit mask): BiCG iteration, its eigBiCG
+// window (restart), BiCGStab iteration. Each kernel skips the slots of the
+// other kind, so a chunk can serve a mix of slots.
+constexpr int CH_BICG = 1, CH_WINDOW = 2, CH_STAB = 4;
+
+lqcd_status enqueue_chunk(lqcd_ctx* c, int nslots, int kinds) {
     const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
     for (int it = 0; it < CHECK_EVERY; ++it) {
-        CK(launch_matvec(c, nslots, c->dslash_variant));
-        if (windowed) {
-            CK(launch_restart_coeffs(c->d_state, c->d_ptrs, nslots, c->eigwork, c->stream));
-            if (c->kprec && c->use_tc && restart_tc_supported(c->m, 2 * c->nev, c->N))
-                CK(launch_restart_tc(c->d_state, c->d_ptrs, nslots, c->N, c->d_err, c->stream));
-            else
-                CK(launch_window_gemm(c->kprec, 2 * c->nev, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+        if (kinds & (CH_BICG | CH_WINDOW)) {
+            CK(launch_matvec(c, nslots, c->dslash_variant));
+            if (kinds & CH_WINDOW) {
+                CK(launch_restart_coeffs(c->d_state, c->d_ptrs, nslots, c->eigwork, c->stream));
+                if (c->kprec && c->use_tc && restart_tc_supported(c->m, 2 * c->nev, c->N))
+                    CK(launch_restart_tc(c->d_state, c->d_ptrs, nslots, c->N, c->d_err, c->stream));
+                else
+                    CK(launch_window_gemm(c->kprec, 2 * c->nev, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+            }
+            CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+            CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N,
+                              c->stream, c->ru_variant, c->links_df));
+            CK(launch_bicg_scalars(c->d_state, c->d_ptrs, nslots, c->stream));
+            CK(launch_bicg_direction(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
         }
-        CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
-        CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream,
-                          c->ru_variant, c->links_df));
-        CK(launch_bicg_scalars(c->d_state, c->d_ptrs, nslots, c->stream));
-        CK(launch_bicg_direction(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+        if (kinds & CH_STAB) {
+            CK(launch_stab_step(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
+            CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N,
+                              c->stream, c->ru_variant, c->links_df));
+            CK(launch_stab_scalars(c->d_state, nslots, c->stream));
+        }
     }
     return LQCD_OK;
 }
 
-lqcd_status run_chunk(lqcd_ctx* c, int nslots, int windowed) {
-    cudaGraphExec_t& ge = c->graphs[nslots][windowed];
+lqcd_status run_chunk(lqcd_ctx* c, int nslots, int kinds) {
+    cudaGraphExec_t& ge = c->graphs[nslots][kinds];
     if (!ge) {
         cudaGraph_t graph = nullptr;
         const long long before = launches_so_far();   // captured launches are not executions
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        lqcd_status s = enqueue_chunk(c, nslots, windowed);
+        lqcd_status s = enqueue_chunk(c, nslots, kinds);
         cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
         set_launches(before);
         if (s != LQCD_OK) { if (graph) cudaGraphDestroy(graph); return s; }
         if (e != cudaSuccess) { set_error("cudaStreamEndCapture", e); return LQCD_ERR_CUDA; }
         size_t nodes = 0;
         cudaGraphGetNodes(graph, nullptr, &nodes);
-        c->graph_nodes[nslots][windowed] = (long long)nodes;
+        c->graph_nodes[nslots][kinds] = (long long)nodes;
         e = cudaGraphInstantiate(&ge, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) { ge = nullptr; set_error("cudaGraphInstantiate", e); return LQCD_ERR_CUDA; }
     }
     CK(cudaGraphLaunch(ge, c->stream));
-    count_launches(c->graph_nodes[nslots][windowed]);
+    count_launches(c->graph_nodes[nslots][kinds]);
     return LQCD_OK;
 }
 
-// Solve the right-hand sides already in slots 0..k-1 (b_all, x_hi_all);
-// windowed = eigBiCG window on. tol_override > 0 replaces the tolerance.
-lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol) {
+// Solve the right-hand sides already in slots 0..k-1 (b_all, x_hi_all) to
+// tolerance tol; windowed = eigBiCG window on. rec_stop: stop at the recursive
+// convergence candidate without reliable updates (the eigBiCG leg of a
+// mixed-precision solve). precise: FP64 starting residual. maxiter[s] (may be
+// null) replaces the iteration limit of slot s; a slot whose limit is 0 sits
+// the solve out (idle).
+lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol, bool rec_stop = false, bool precise = false,
+                        const int* maxiter = nullptr, bool stab = false) {
     for (int s = 0; s < c->kmax; ++s) {
         SlotState& st = c->h_state[s];
         memset(&st, 0, sizeof(SlotState));
-        st.status = s < k ? ST_RUNNING : ST_IDLE;
+        st.maxiter = maxiter && s < k ? maxiter[s] : c->p.maxiter;
+        st.status = s < k && st.maxiter > 0 ? ST_RUNNING : ST_IDLE;
         st.tol = tol;
-        st.maxiter = c->p.maxiter;
-        st.delta = c->kprec ? c->p.delta : 0.0;
+        st.delta = c->kprec && !rec_stop ? c->p.delta : 0.0;
+        st.rec_stop = rec_stop ? 1 : 0;
         st.m = windowed ? c->m : 0;
         st.nev = c->nev;
+        st.g5 = c->p.gamma5;
+        st.stab = stab && !windowed ? 1 : 0;
     }
     CK(cudaMemcpyAsync(c->d_state, c->h_state, sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
     // r0 = b - A x0 (FP64), then the Krylov start vectors
-    lqcd_status s = residual_fields(c, k, c->x_hi_all, c->rt_all, c->b_all);
+    lqcd_status s = residual_fields(c, k, c->x_hi_all, c->rt_all, c->b_all, precise);
     if (s != LQCD_OK) return s;
     CK(launch_bicg_start(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
     while (true) {
@@ -775,7 +932,7 @@ lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol) {
         bool any = false;
         for (int j = 0; j < k; ++j) any = any || c->h_state[j].status == ST_RUNNING;
         if (!any) break;
-        s = run_chunk(c, k, windowed);
+        s = run_chunk(c, k, stab && !windowed ? CH_STAB : (windowed ? CH_BICG | CH_WINDOW : CH_BICG));
         if (s != LQCD_OK) return s;
     }
     CK(launch_bicg_finish(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream,
@@ -849,11 +1006,26 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx* c, int k, const double* b, double* x
         return LQCD_ERR_STATE;
     }
     lqcd_status worst = LQCD_OK;
-    for (int j0 = 0; j0 < k; j0 += c->kmax) {
+    for (int j0 = 0, kb = 0; j0 < k; j0 += kb) {
         auto t0 = std::chrono::steady_clock::now();
-        const int kb = std::min(c->kmax, k - j0);
+        kb = std::min(c->kbatch, k - j0);
         lqcd_mode md = mode;
         if (md == LQCD_MODE_AUTO) md = c->eig_rhs_done < c->p.n1 ? LQCD_MODE_EIGBICG : LQCD_MODE_DEFLATED;
+        if (md == LQCD_MODE_EIGBICG) {
+            // windows for as many sources of the batch as the memory plan admits
+            int got = 0;
+            for (; got < kb; ++got) {
+                bool ok = false;
+                lqcd_status s = attach_window(c, got, &ok);
+                if (s != LQCD_OK) return s;
+                if (!ok) break;
+            }
+            if (got == 0) {
+                g_last_error = "no device memory (or hbm_budget_bytes) for an eigBiCG window";
+                return LQCD_ERR_OOM;
+            }
+            kb = got;
+        }
         lqcd_status s = upload(c, b + (size_t)j0 * 2 * c->N, kb, c->b_all, 0, on_device);
         if (s != LQCD_OK) return s;
         s = upload(c, x + (size_t)j0 * 2 * c->N, kb, c->x_hi_all, 0, on_device);
@@ -868,19 +1040,55 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx* c, int k, const double* b, double* x
         if (windowed) c->last_window_valid = 0;
         if (md == LQCD_MODE_DEFLATED && c->p.deftol > c->p.tol && c->n_def > 0) {
             // DefTol restart: solve to deftol, re-deflate, solve to tol
-            s = solve_slots(c, kb, 0, c->p.deftol);
+            s = solve_slots(c, kb, 0, c->p.deftol, false, false, nullptr, c->p.bicgstab != 0);
             if (s != LQCD_OK) return s;
             first.assign(c->h_state, c->h_state + kb);
-            s = deflate_slots(c, kb);
+            s = deflate_slots(c, kb, c->kprec != 0);
             if (s != LQCD_OK) return s;
             outer = 1;
         }
-        s = solve_slots(c, kb, windowed ? 1 : 0, c->p.tol);
+        // Mixed-precision eigBiCG runs in two legs: the windowed iteration without
+        // reliable updates (replacing r by the true residual would break the
+        // Lanczos relation W^H A V = H of the window) until the recursive residual
+        // reaches tol; its Ritz vectors grow the eigenspace; then a deflated
+        // correction leg from the FP64 residual, with reliable updates, to tol.
+        const bool two_leg = windowed && c->kprec;
+        s = solve_slots(c, kb, windowed ? 1 : 0, c->p.tol, two_leg, outer > 0 && c->kprec, nullptr,
+                        c->p.bicgstab != 0);
         if (s != LQCD_OK) return s;
         std::vector<SlotState> fin(c->h_state, c->h_state + kb);
         if (windowed) {
             s = grow_from_windows(c, kb);
             if (s != LQCD_OK) return s;
+            for (int j = 0; j < kb; ++j) {
+                s = detach_window(c, j);
+                if (s != LQCD_OK) return s;
+            }
+        }
+        if (two_leg) {
+            first = fin;
+            std::vector<int> left(kb, 0);
+            for (int j = 0; j < kb; ++j)
+                if (first[j].status == ST_CONVERGED) left[j] = std::max(c->p.maxiter - first[j].iter, 0);
+            if (std::count(left.begin(), left.end(), 0) == 0) {
+                s = deflate_slots(c, kb, true);
+            } else {   // a slot whose first leg failed keeps its iterate
+                for (int j = 0; j < kb && s == LQCD_OK; ++j)
+                    if (left[j] > 0) s = deflate_range(c, j, 1, true);
+            }
+            if (s != LQCD_OK) return s;
+            s = solve_slots(c, kb, 0, c->p.tol, false, true, left.data());
+            if (s != LQCD_OK) return s;
+            outer = 1;
+            for (int j = 0; j < kb; ++j) {
+                if (left[j] > 0) {
+                    const int restarts = first[j].restarts;
+                    fin[j] = c->h_state[j];
+                    fin[j].restarts = restarts;
+                } else {
+                    first[j] = SlotState{};   // the first leg stopped short: report it alone
+                }
+            }
         }
         s = download(c, c->x_hi_all, 0, kb, x + (size_t)j0 * 2 * c->N, on_device);
         if (s != LQCD_OK) return s;
@@ -974,7 +1182,12 @@ extern "C" lqcd_status lqcd_eigs(lqcd_ctx* c, int* n_inout, double* evals, doubl
     if (n == 0) return LQCD_ERR_STATE;
     const int nout = std::min(*n_inout, n);
     const int ld = c->n_def_max;
-    // G = M^{-1} H  (n x n, ld n) ; eig(G) -> lam, Y, Zhat ; left vectors z = M^{-H} zhat
+    // Pencil (H, M) with P M = L U: G = L^{-1} P H U^{-1} (n x n, ld n), eig(G) ->
+    // lam, Yhat, Zhat; right vectors y = U^{-1} yhat, left z = P^T L^{-H} zhat.
+    // The two-sided form splits M's conditioning between the factors (the
+    // accumulated bases are nearly dependent: cond(M) reaches 1e13) and keeps the
+    // eigenvalues at the accuracy of a QZ solve of the pencil, where M^{-1} H loses
+    // three or more digits.
     double2* G = c->dsmall;
     double2* Y = G + (size_t)n * n;
     double2* Z = Y + (size_t)n * n;
@@ -997,9 +1210,11 @@ extern "C" lqcd_status lqcd_eigs(lqcd_ctx* c, int* n_inout, double* evals, doubl
     copy_block_kernel<<<64, 256, 0, c->stream>>>(Hp, ldp, G, n, n, n);
     count_launches(1);
     CK(cudaGetLastError());
-    CK(launch_lu_solve(n, Mp, ldp, Mpiv, 0, n, G, n, c->stream));
+    CK(launch_lu_part(n, Mp, ldp, Mpiv, LU_LEFT_PL, n, G, n, c->stream));
+    CK(launch_lu_part(n, Mp, ldp, Mpiv, LU_RIGHT_U, n, G, n, c->stream));
     CK(launch_small_eig(n, G, n, n, lam, Y, Z, n, c->dinfo + 16, c->eigwork, c->stream));
-    CK(launch_lu_solve(n, Mp, ldp, Mpiv, 1, n, Z, n, c->stream));
+    CK(launch_lu_part(n, Mp, ldp, Mpiv, LU_LEFT_U, n, Y, n, c->stream));
+    CK(launch_lu_part(n, Mp, ldp, Mpiv, LU_LEFT_LH, n, Z, n, c->stream));
     std::vector<double2> hl(n);
     CK(cudaMemcpyAsync(hl.data(), lam, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1008,13 +1223,13 @@ extern "C" lqcd_status lqcd_eigs(lqcd_ctx* c, int* n_inout, double* evals, doubl
     std::vector<double> hres(nout, 0.0);
     for (int j0 = 0; j0 < nout; j0 += c->kmax) {
         const int kb = std::min(c->kmax, nout - j0);
-        CK(launch_vupdate(n, c->Ur, c->kprec, Y + j0, n, kb, c->x_hi_all, 0, 1, c->N, c->stream));
+        CK(launch_vupdate(n, c->Ur, c->kprec, Y + j0, n, kb, c->x_hi_all, 0, 1, c->N, c->stream, 1));
         if (evecs_r) {
             lqcd_status s = download(c, c->x_hi_all, 0, kb, evecs_r + (size_t)j0 * 2 * c->N, 0);
             if (s != LQCD_OK) return s;
         }
         if (evecs_l) {
-            CK(launch_vupdate(n, c->Ul, c->kprec, Z + j0, n, kb, c->rt_all, 0, 1, c->N, c->stream));
+            CK(launch_vupdate(n, c->Ul, c->kprec, Z + j0, n, kb, c->rt_all, 0, 1, c->N, c->stream, 1));
             lqcd_status s = download(c, c->rt_all, 0, kb, evecs_l + (size_t)j0 * 2 * c->N, 0);
             if (s != LQCD_OK) return s;
         }
@@ -1191,7 +1406,9 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
         (kernel >= 10 + matvec_variants() && kernel != TIME_TILED && !(kernel >= 40 && kernel < 40 + true_resid_variants())))
         return LQCD_ERR_ARG;
     if (kernel == TIME_TILED && !c->tile_ok[k]) return LQCD_ERR_ARG;
-    if (kernel >= 10 && kernel < 10 + matvec_variants() && !matvec_variant_ok(c->g, kernel - 10)) return LQCD_ERR_ARG;
+    if (kernel >= 10 && kernel < 10 + matvec_variants() &&
+        !(c->p.gamma5 ? matvec_g5_variant_ok(c->g, kernel - 10) : matvec_variant_ok(c->g, kernel - 10)))
+        return LQCD_ERR_ARG;
     const int ru_saved = c->ru_variant;
     if (kernel >= 40 && kernel < 40 + true_resid_variants()) {   // reliable update with FP64 shape v
         c->ru_variant = kernel - 40;
@@ -1211,6 +1428,7 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
         st.rnorm = 1.0; st.bnorm = 1.0; st.rmax = 1.0; st.r_ru = 1.0;
         st.alpha = make_double2(0.1, 0.0);
         st.beta = make_double2(0.1, 0.0);
+        st.g5 = c->p.gamma5;
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -1220,9 +1438,9 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
     for (int r = 0; r < reps; ++r) {
         CK(cudaMemcpyAsync(c->d_state, tmpl.data(), sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
         CK(cudaEventRecord(e0, c->stream));
-        if (kernel == 0) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->stream,
-                                               c->dslash_variant));
+        if (kernel == 0) CK(launch_matvec(c, k, c->dslash_variant));
         else if (kernel == TIME_TILED) CK(launch_matvec(c, k, TILED));
+        else if (kernel >= 10 && c->p.gamma5) CK(launch_matvec(c, k, kernel - 10));
         else if (kernel >= 10) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k,
                                                      c->stream, kernel - 10));
         else if (kernel == 1) CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
@@ -1261,7 +1479,7 @@ extern "C" lqcd_status lqcd_set_tensor_cores(lqcd_ctx* c, int on) {
     CK(cudaStreamSynchronize(c->stream));
     c->use_tc = on ? 1 : 0;
     for (int i = 0; i <= MAX_SLOTS; ++i)   // the iteration graphs hold the old kernels
-        for (int j = 0; j < 2; ++j)
+        for (int j = 0; j < 8; ++j)
             if (c->graphs[i][j]) {
                 cudaGraphExecDestroy(c->graphs[i][j]);
                 c->graphs[i][j] = nullptr;
@@ -1290,7 +1508,10 @@ static lqcd_status autotune(lqcd_ctx* c) {
     double best = 1e300;
     for (int v = 0; v < nv; ++v) {
         double ms = 0.0;
-        if (!matvec_variant_ok(c->g, v)) { c->tune_ms[v] = -1.0; continue; }
+        if (!(c->p.gamma5 ? matvec_g5_variant_ok(c->g, v) : matvec_variant_ok(c->g, v))) {
+            c->tune_ms[v] = -1.0;
+            continue;
+        }
         lqcd_status s = time_kernel_impl(c, 10 + v, c->kmax, 1, &ms);   // warm-up
         if (s != LQCD_OK) return s;
         s = time_kernel_impl(c, 10 + v, c->kmax, 3, &ms);
@@ -1319,6 +1540,47 @@ static lqcd_status autotune(lqcd_ctx* c) {
     return LQCD_OK;
 }
 
+// Batch-size autotuner (k_max = 0): time one BiCG iteration (operator, residual
+// update, direction update) over k = 1, 2, 4, 8 slots and keep the k with the most
+// right-hand sides per second (ties to the larger k, which needs fewer launches).
+static lqcd_status autotune_batch(lqcd_ctx* c) {
+    double best = 0.0;
+    int kbest = c->kmax;
+    for (int k = 1; k <= c->kmax; k *= 2) {
+        double t = 0.0;
+        for (int kernel = 0; kernel < 3; ++kernel) {
+            double ms = 0.0;
+            lqcd_status s = time_kernel_impl(c, kernel, k, 1, &ms);   // warm-up
+            if (s != LQCD_OK) return s;
+            s = time_kernel_impl(c, kernel, k, 3, &ms);
+            if (s != LQCD_OK) return s;
+            t += ms;
+        }
+        c->k_ms[k] = t;
+        const double rate = k / t;
+        if (rate >= best * 0.99) { best = std::max(best, rate); kbest = k; }
+    }
+    c->kbatch = kbest;
+    return LQCD_OK;
+}
+
+extern "C" int lqcd_batch_size(const lqcd_ctx* c) { return c ? c->kbatch : 0; }
+
+extern "C" lqcd_status lqcd_memory_info(const lqcd_ctx* c, size_t* plan_bytes, size_t* window_bytes,
+                                        int* windows_attached) {
+    if (!c) return LQCD_ERR_ARG;
+    if (plan_bytes) *plan_bytes = c->plan_bytes;
+    if (window_bytes) *window_bytes = c->win_bytes;
+    if (windows_attached) *windows_attached = c->win_attached;
+    return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_batch_timings(const lqcd_ctx* c, double* ms) {
+    if (!c || !ms) return LQCD_ERR_ARG;
+    for (int k = 0; k <= MAX_SLOTS; ++k) ms[k] = c->k_ms[k];
+    return c->k_auto ? LQCD_OK : LQCD_ERR_STATE;
+}
+
 // ============================================================ pair-kernel hook
 extern "C" lqcd_status lqcd_apply_pair(lqcd_ctx* c, int variant, int k, const double* p, const double* phat,
                                        double* Ap, double* Ahp, double* sigma) {
@@ -1326,7 +1588,7 @@ extern "C" lqcd_status lqcd_apply_pair(lqcd_ctx* c, int variant, int k, const do
     if (variant == TILED) {
         if (!c->tile_ok[k]) return LQCD_ERR_ARG;
     } else if (variant < 0 || variant >= matvec_variants() || (!c->kprec && variant != 0) ||
-               !matvec_variant_ok(c->g, variant)) {
+               !(c->p.gamma5 ? matvec_g5_variant_ok(c->g, variant) : matvec_variant_ok(c->g, variant))) {
         return LQCD_ERR_ARG;
     }
     const size_t fb = 2 * c->N;   // doubles per host field
@@ -1341,6 +1603,8 @@ extern "C" lqcd_status lqcd_apply_pair(lqcd_ctx* c, int variant, int k, const do
         memset(&tmpl[s], 0, sizeof(SlotState));
         tmpl[s].status = s < k ? ST_RUNNING : ST_IDLE;
         tmpl[s].rho = make_double2(1.0, 0.0);
+        tmpl[s].g5 = c->p.gamma5;
+        tmpl[s].m = c->p.gamma5 ? 1 : 0;   // gamma5 shapes then also store A^+ phat = gamma5 A p
     }
     CK(cudaMemcpyAsync(c->d_state, tmpl.data(), sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
     CK(launch_matvec(c, k, variant));
@@ -1372,23 +1636,30 @@ namespace {
 
 // One BiCG run in slot s from the x_hi and b already there: deflation of the
 // initial guess (phases 1 and 2 of Alg. Incremental eigBiCG), initial residual
-// and start vectors, with tolerance tol.
-lqcd_status begin_slot(lqcd_ctx* c, int s, lqcd_mode md, double tol) {
+// and start vectors, with tolerance tol. windowed: eigBiCG window on;
+// rec_stop: the eigBiCG leg of a mixed-precision solve (no reliable updates,
+// stop at the recursive convergence candidate); precise: FP64 residuals for
+// the deflation and the start (a leg that continues from an earlier iterate).
+lqcd_status begin_slot(lqcd_ctx* c, int s, lqcd_mode md, double tol, bool windowed, bool rec_stop, bool precise,
+                       int maxiter, bool stab = false) {
     if (md != LQCD_MODE_PLAIN && c->n_def > 0) {
-        lqcd_status r = deflate_range(c, s, 1);
+        lqcd_status r = deflate_range(c, s, 1, precise);
         if (r != LQCD_OK) return r;
     }
     SlotState& st = c->h_state[s];
     memset(&st, 0, sizeof(SlotState));
     st.status = ST_RUNNING;
     st.tol = tol;
-    st.maxiter = c->p.maxiter;
-    st.delta = c->kprec ? c->p.delta : 0.0;
-    st.m = md == LQCD_MODE_EIGBICG ? c->m : 0;
+    st.maxiter = maxiter;
+    st.delta = c->kprec && !rec_stop ? c->p.delta : 0.0;
+    st.rec_stop = rec_stop ? 1 : 0;
+    st.m = windowed ? c->m : 0;
     st.nev = c->nev;
+    st.g5 = c->p.gamma5;
+    st.stab = stab && !windowed ? 1 : 0;
     CK(cudaMemcpyAsync(c->d_state + s, &st, sizeof(SlotState), cudaMemcpyHostToDevice, c->stream));
     lqcd_status r = residual_fields(c, 1, c->x_hi_all + (size_t)s * c->N, c->rt_all + (size_t)s * c->N,
-                                    c->b_all + (size_t)s * c->N);
+                                    c->b_all + (size_t)s * c->N, precise);
     if (r != LQCD_OK) return r;
     CK(launch_bicg_start(c->g, c->links64, c->p.kappa, c->kprec, c->d_state + s, c->d_ptrs + s, 1, c->N, c->stream));
     return LQCD_OK;
@@ -1397,23 +1668,25 @@ lqcd_status begin_slot(lqcd_ctx* c, int s, lqcd_mode md, double tol) {
 // Start request req in free slot s. A deflated request with deftol > tol first
 // runs to deftol, is deflated again and then runs to tol (the DefTol restart),
 // exactly as lqcd_solve does.
-lqcd_status admit(lqcd_ctx* c, int s, const lqcd_ctx::Request& req) {
+lqcd_status admit(lqcd_ctx* c, int s, const lqcd_ctx::Request& req, lqcd_mode md) {
     lqcd_ctx::SlotJob& job = c->jobs[s];
-    lqcd_mode md = req.mode;
-    if (md == LQCD_MODE_AUTO) md = c->eig_rhs_done + c->eig_inflight < c->p.n1 ? LQCD_MODE_EIGBICG : LQCD_MODE_DEFLATED;
     lqcd_status r = upload(c, req.b, 1, c->b_all + (size_t)s * c->N, 0, req.on_device);
     if (r != LQCD_OK) return r;
     r = upload(c, req.x, 1, c->x_hi_all + (size_t)s * c->N, 0, req.on_device);
     if (r != LQCD_OK) return r;
     const bool two_legs = md == LQCD_MODE_DEFLATED && c->p.deftol > c->p.tol && c->n_def > 0;
-    r = begin_slot(c, s, md, two_legs ? c->p.deftol : c->p.tol);
+    const bool windowed = md == LQCD_MODE_EIGBICG;
+    const bool eig_legs = windowed && c->kprec;   // mixed eigBiCG: window leg, then correction leg
+    r = begin_slot(c, s, md, two_legs ? c->p.deftol : c->p.tol, windowed, eig_legs, false, c->p.maxiter,
+                   c->p.bicgstab != 0);
     if (r != LQCD_OK) return r;
     job.busy = true;
     job.req = req;
     job.md = md;
-    job.windowed = md == LQCD_MODE_EIGBICG;
+    job.windowed = windowed;
     job.deftol_pending = two_legs;
-    job.first_iters = job.first_matvecs = job.first_ru = job.outer = 0;
+    job.correction_pending = eig_legs;
+    job.first_iters = job.first_matvecs = job.first_ru = job.first_restarts = job.outer = 0;
     job.t0 = std::chrono::steady_clock::now();
     if (job.windowed) c->eig_inflight += 1;
     return LQCD_OK;
@@ -1435,13 +1708,30 @@ lqcd_status retire(lqcd_ctx* c, int s) {
         job.first_ru = f.ru_count;
         job.outer = 1;
         job.deftol_pending = false;
-        return begin_slot(c, s, job.md, c->p.tol);
+        return begin_slot(c, s, job.md, c->p.tol, false, false, c->kprec != 0, c->p.maxiter, c->p.bicgstab != 0);
     }
     if (job.windowed) {
         lqcd_status r = grow_slot(c, s);
         if (r != LQCD_OK) return r;
         c->last_window_valid = 1;
         c->eig_inflight -= 1;
+        job.windowed = false;
+        r = detach_window(c, s);   // its memory is free for the next eigBiCG request
+        if (r != LQCD_OK) return r;
+    }
+    if (job.correction_pending) {
+        // mixed eigBiCG: the window leg stopped at the recursive tolerance; the
+        // deflated correction leg (FP64 residual, reliable updates) finishes it
+        const SlotState f = c->h_state[s];
+        job.correction_pending = false;
+        if (f.status == ST_CONVERGED && f.iter < c->p.maxiter) {
+            job.first_iters = f.iter;
+            job.first_matvecs = f.matvecs;
+            job.first_ru = f.ru_count;
+            job.first_restarts = f.restarts;
+            job.outer = 1;
+            return begin_slot(c, s, LQCD_MODE_DEFLATED, c->p.tol, false, false, true, c->p.maxiter - f.iter);
+        }
     }
     lqcd_status r = download(c, c->x_hi_all + (size_t)s * c->N, 0, 1, job.req.x, job.req.on_device);
     if (r != LQCD_OK) return r;
@@ -1451,7 +1741,7 @@ lqcd_status retire(lqcd_ctx* c, int s) {
     memset(&f.info, 0, sizeof(f.info));
     f.info.iters = st.iter + job.first_iters;
     f.info.matvecs = st.matvecs + job.first_matvecs;
-    f.info.restarts = st.restarts;
+    f.info.restarts = st.restarts + job.first_restarts;
     f.info.reliable_updates = st.ru_count + job.first_ru;
     f.info.outer_steps = job.outer;
     f.info.true_resid = st.bnorm > 0 ? st.true_rnorm / st.bnorm : 0.0;
@@ -1515,24 +1805,53 @@ extern "C" lqcd_status lqcd_progress(lqcd_ctx* c, int wait, int* pending) {
             lqcd_status r = retire(c, s);
             if (r != LQCD_OK) return r;
         }
-    // 3. admit queued requests into free slots
-    for (int s = 0; s < c->kmax && !c->queue.empty(); ++s)
-        if (!c->jobs[s].busy) {
-            lqcd_ctx::Request req = c->queue.front();
-            c->queue.pop_front();
-            lqcd_status r = admit(c, s, req);
+    // 3. admit queued requests into free slots, in arrival order, by device memory:
+    // an eigBiCG request needs a window (attach_window); one that does not fit now
+    // waits for memory to free up while later requests that need no window pass it.
+    // If no window is held (nothing will free), AUTO requests run deflated and
+    // explicit eigBiCG requests finish with LQCD_ERR_OOM.
+    for (int s = 0; s < c->kbatch && !c->queue.empty(); ++s) {
+        if (c->jobs[s].busy) continue;
+        for (auto it = c->queue.begin(); it != c->queue.end(); ++it) {
+            lqcd_mode md = it->mode;
+            if (md == LQCD_MODE_AUTO)
+                md = c->eig_rhs_done + c->eig_inflight < c->p.n1 ? LQCD_MODE_EIGBICG : LQCD_MODE_DEFLATED;
+            if (md == LQCD_MODE_EIGBICG) {
+                bool ok = false;
+                lqcd_status r = attach_window(c, s, &ok);
+                if (r != LQCD_OK) return r;
+                if (!ok) {
+                    if (c->win_attached > 0) continue;   // wait for a window to be freed
+                    if (it->mode == LQCD_MODE_AUTO) {
+                        md = LQCD_MODE_DEFLATED;
+                    } else {
+                        lqcd_ctx::Finished f;
+                        memset(&f.info, 0, sizeof(f.info));
+                        f.info.mode_used = LQCD_MODE_EIGBICG;
+                        f.status = LQCD_ERR_OOM;
+                        c->finished[it->ticket] = f;
+                        c->queue.erase(it);
+                        --s;   // the slot is still free
+                        break;
+                    }
+                }
+            }
+            const lqcd_ctx::Request req = *it;
+            c->queue.erase(it);
+            lqcd_status r = admit(c, s, req, md);
             if (r != LQCD_OK) return r;
+            break;
         }
+    }
     // 4. next chunk of iterations for every busy slot (asynchronous)
-    int busy = 0;
-    bool win = false;
+    int busy = 0, kinds = 0;
     for (int s = 0; s < c->kmax; ++s)
         if (c->jobs[s].busy) {
             ++busy;
-            win = win || c->jobs[s].windowed;
+            kinds |= c->h_state[s].stab ? CH_STAB : (c->jobs[s].windowed ? CH_BICG | CH_WINDOW : CH_BICG);
         }
     if (busy) {
-        lqcd_status r = run_chunk(c, c->kmax, win ? 1 : 0);
+        lqcd_status r = run_chunk(c, c->kmax, kinds);
         if (r != LQCD_OK) return r;
         if (!c->chunk_ev) CK(cudaEventCreateWithFlags(&c->chunk_ev, cudaEventDisableTiming));
         CK(cudaEventRecord(c->chunk_ev, c->stream));

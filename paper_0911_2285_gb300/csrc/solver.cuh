@@ -39,7 +39,14 @@ struct SlotState {
     int live;             // 1 while the slot takes part in the current iteration
     int x_owed;           // 1: x_lo has not yet received alpha p of the last residual update
     int x_dir;            // 1: the direction update adds alpha p to x_lo in this iteration
-    int pad;
+    int rec_stop;         // 1: stop at the first recursive convergence candidate, without
+                          // replacing r (the eigBiCG leg of a mixed-precision solve)
+    int g5;               // 1: gamma5-Hermitian variant (Sec. 4): rhat = gamma5 r, phat = gamma5 p,
+                          // A^+ phat = gamma5 A p; one operator product per iteration
+    int stab;             // 1: BiCGStab iteration (phase-2 solver of Alg. Incremental eigBiCG)
+    double2 omega;        // BiCGStab: omega_j of the minimal-residual step
+    double2 ts;           // BiCGStab: (t, s) of the current step
+    double tt;            // BiCGStab: (t, t)
 };
 
 // Device pointers of one slot. Krylov vectors are in the precision of the

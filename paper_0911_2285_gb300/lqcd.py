@@ -44,6 +44,8 @@ class Params(C.Structure):
         ("hbm_budget_bytes", C.c_size_t),
         ("n_def_max", C.c_int),
         ("delta", C.c_double),
+        ("gamma5", C.c_int),
+        ("bicgstab", C.c_int),
     ]
 
 
@@ -113,6 +115,12 @@ def lib():
         L.lqcd_small_eig_noalloc.restype = C.c_int
         L.lqcd_apply_pair.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
         L.lqcd_apply_pair.restype = C.c_int
+        L.lqcd_memory_info.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), ip]
+        L.lqcd_memory_info.restype = C.c_int
+        L.lqcd_batch_size.argtypes = [vp]
+        L.lqcd_batch_size.restype = C.c_int
+        L.lqcd_batch_timings.argtypes = [vp, dp]
+        L.lqcd_batch_timings.restype = C.c_int
         L.lqcd_set_wait_limit.argtypes = [C.c_longlong]
         L.lqcd_set_wait_limit.restype = C.c_int
         L.lqcd_wait_flag.argtypes = [vp, vp]
@@ -181,7 +189,7 @@ class Solver:
 
     def __init__(self, links, dims, kappa, nev=10, m=40, n1=4, tol=1e-10, maxiter=5000,
                  precision="mixed", deftol=0.0, k_max=0, hbm_budget_bytes=0, n_def_max=0,
-                 delta=0.0, stream=None):
+                 delta=0.0, stream=None, gamma5=False, bicgstab=False):
         links = np.ascontiguousarray(links, dtype=np.complex128)
         self.dims = tuple(int(d) for d in dims)
         self.kappa = float(kappa)
@@ -201,7 +209,10 @@ class Solver:
         p.hbm_budget_bytes = hbm_budget_bytes
         p.n_def_max = n_def_max
         p.delta = delta
+        p.gamma5 = 1 if gamma5 else 0
+        p.bicgstab = 1 if bicgstab else 0
         self.params = p
+        self.gamma5 = bool(gamma5)
         self.precision = precision
         h = C.c_void_p()
         st = lib().lqcd_eigbicg_init(C.byref(h), C.byref(p), C.c_void_p(links.ctypes.data),
@@ -209,6 +220,24 @@ class Solver:
         _check(st, "lqcd_eigbicg_init")
         self._h = h
         self.kmax = k_max or 8
+
+    def memory_info(self):
+        """``(plan_bytes, window_bytes, windows_attached)``: the fixed device-memory plan,
+        the size of one eigBiCG window and the windows held now."""
+        plan, win, att = C.c_size_t(), C.c_size_t(), C.c_int()
+        _check(lib().lqcd_memory_info(self._h, C.byref(plan), C.byref(win), C.byref(att)), "lqcd_memory_info")
+        return plan.value, win.value, att.value
+
+    def batch_size(self):
+        """Right-hand sides per batched launch (``k_max``, or the autotuned size)."""
+        return lib().lqcd_batch_size(self._h)
+
+    def batch_timings(self):
+        """ms of one BiCG iteration per batch size k (index k) as the batch-size autotuner
+        timed it (``k_max = 0`` contexts only; else None)."""
+        ms = (C.c_double * 9)()
+        st = lib().lqcd_batch_timings(self._h, ms)
+        return list(ms) if st == OK else None
 
     def close(self):
         if getattr(self, "_h", None):

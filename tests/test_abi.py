@@ -67,6 +67,6 @@ def test_init_refuses_a_plan_above_the_hbm_budget_without_touching_the_device(li
     links = np.zeros(int(np.prod(dims)) * 36, dtype=np.complex128)
     with pytest.raises(L.LQCDError) as e:
         L.Solver(links, dims, 0.12, nev=8, m=24, tol=1e-10, precision="mixed", k_max=8,
-                 hbm_budget_bytes=64 << 20)
+                 hbm_budget_bytes=8 << 20)
     assert e.value.status == L.ERR_OOM
     assert "budget" in L.last_error()

@@ -152,3 +152,69 @@ def test_session_edge_cases():
         s.set_tensor_cores(True)   # free again
     assert res[tz][1] == lqcd.OK and np.all(xz == 0)
     assert res[tb][1] == lqcd.ERR_NOCONV and res[tb][0]["iters"] == 6
+
+
+def test_admission_by_device_memory_queues_and_admits_as_windows_free():
+    """hbm_budget_bytes with room for the fixed plan and one eigBiCG window: of three
+    eigBiCG requests only one holds a window at a time, the others wait in the queue
+    (no error) while a plain request submitted after them is admitted past them;
+    each waiting request is admitted when the window before it is released, and
+    every request finishes with the FP64 residual."""
+    from paper_0911_2285_gb300 import lqcd
+    s0, op, w = solver("8^4", n1=3)
+    with s0:
+        plan, win, att = s0.memory_info()
+    assert att == 0 and win > 0
+    s, op, w = solver("8^4", n1=3, hbm_budget_bytes=plan + win + win // 2)
+    srcs = [z2_source(w["dims"], 8500 + i) for i in range(4)]
+    xs = [np.zeros_like(b) for b in srcs]
+    with s:
+        tickets = [s.submit(srcs[i], xs[i], mode="eigbicg") for i in range(3)]
+        tickets.append(s.submit(srcs[3], xs[3], mode="plain"))
+        s.progress()
+        assert s.memory_info()[2] == 1
+        done, seen, max_att = {}, 0, 0
+        for _ in range(100000):
+            pending = s.progress()
+            max_att = max(max_att, s.memory_info()[2])
+            for t in tickets:
+                if t not in done:
+                    d, info, st = s.poll(t)
+                    if d:
+                        done[t] = (info, st)
+            if len(done) == 4 and pending == 0:
+                break
+        else:
+            raise AssertionError("session did not drain")
+        assert s.memory_info()[2] == 0
+    assert max_att == 1
+    # the plain request, submitted last, finished before the last eigBiCG one
+    order = list(done)
+    assert order.index(tickets[3]) < order.index(tickets[2])
+    for i, t in enumerate(tickets):
+        info, st = done[t]
+        assert st == lqcd.OK
+        assert info["mode_used"] == (1 if i < 3 else 3)
+        assert true_resid(op, srcs[i], xs[i]) <= 1e-10
+
+
+def test_budget_without_room_for_a_window():
+    """A budget that holds the fixed plan but no eigBiCG window: an explicit eigBiCG
+    request finishes with LQCD_ERR_OOM, an AUTO request runs deflated BiCG instead,
+    and a batched eigBiCG solve returns LQCD_ERR_OOM."""
+    from paper_0911_2285_gb300 import lqcd
+    s0, op, w = solver("8^4")
+    with s0:
+        plan, win, _ = s0.memory_info()
+    s, op, w = solver("8^4", hbm_budget_bytes=plan + win // 2)
+    b = z2_source(w["dims"], 8600)
+    with s:
+        x1, x2 = np.zeros_like(b), np.zeros_like(b)
+        t1 = s.submit(b, x1, mode="eigbicg")
+        t2 = s.submit(b, x2, mode="auto")
+        res = drain(s, [t1, t2])
+        assert res[t1][1] == lqcd.ERR_OOM
+        assert res[t2][1] == lqcd.OK and res[t2][0]["mode_used"] == 2
+        assert true_resid(op, b, x2) <= 1e-10
+        _, _, st = s.solve(b, mode="eigbicg", raise_on_fail=False)
+        assert st == lqcd.ERR_OOM

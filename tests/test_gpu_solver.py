@@ -271,3 +271,24 @@ def test_eigenspace_checkpoint_resume(tmp_path):
     with Solver(links, w["dims"], 0.11, nev=w["nev"], m=w["m"], precision="mixed", k_max=1) as s3:
         with pytest.raises(ValueError):
             s3.load_eigenspace(path)
+
+
+def test_batch_size_autotuner_picks_the_fastest_rate_and_is_used():
+    """k_max = 0: init times one BiCG iteration on 1, 2, 4, 8 slots and keeps the
+    batch size with the most right-hand sides per second; lqcd_solve then runs the
+    sources in batches of that size (sources of one batch share its wall time)."""
+    from paper_0911_2285_gb300 import Solver
+    w, links, op = workload("8^4")
+    with Solver(links, w["dims"], w["kappa"], nev=w["nev"], m=w["m"], tol=1e-10, precision="mixed",
+                k_max=0) as s:
+        k = s.batch_size()
+        ms = s.batch_timings()
+        rates = {kk: kk / ms[kk] for kk in (1, 2, 4, 8)}
+        assert all(ms[kk] > 0 for kk in rates)
+        assert k in rates and rates[k] >= 0.99 * max(rates.values()), (k, rates)
+        srcs = np.stack([z2_source(w["dims"], 9100 + i) for i in range(k + 1)])
+        x, info, _ = s.solve(srcs, mode="plain")
+    secs = [i["seconds"] for i in info]
+    assert len(set(secs[:k])) == 1 and secs[k] != secs[0]
+    for i in range(k + 1):
+        assert true_resid(op, srcs[i], x[i]) <= 1e-10

@@ -95,8 +95,9 @@ def test_rejects_unsupported_shape():
 
 def test_restart_product_tensor_cores_match_cuda_cores():
     """eigBiCG with restarts in mixed precision (8^4, m = 40, nev = 10): the window
-    product never feeds back into the BiCG iterates, so both paths give the same x bit
-    for bit and the same iteration and restart counts, and both meet the FP64 true
+    product never feeds back into the BiCG iterates of the window leg, so both paths
+    restart equally often; the correction leg deflates with the Ritz vectors each path
+    built, so the total iteration counts agree to a few and both meet the FP64 true
     residual with the oracle's A. Stopped just after the first restart, the projected
     window matrix H (restart Ritz values plus the coupling row and column formed from
     the new basis vectors) agrees between the paths to FP32 rounding."""
@@ -120,10 +121,10 @@ def test_restart_product_tensor_cores_match_cuda_cores():
             s.solve(b, mode="eigbicg", raise_on_fail=False)   # the second solve starts from a fresh window
             early[tc] = s.last_window()
     (x1, i1, n1), (x0, i0, n0) = full[True], full[False]
-    assert i1["iters"] == i0["iters"] and i1["restarts"] == i0["restarts"] and i1["restarts"] >= 3
+    assert i1["restarts"] == i0["restarts"] and i1["restarts"] >= 3
     assert n1 == n0
-    assert np.array_equal(x1, x0)
-    assert true_resid(op, b, x1) <= 1e-10
+    assert abs(i1["iters"] - i0["iters"]) <= 3 and i1["outer_steps"] == i0["outer_steps"] == 1
+    assert true_resid(op, b, x1) <= 1e-10 and true_resid(op, b, x0) <= 1e-10
     (H1, _, r1), (H0, _, r0) = early[True], early[False]
     assert r1 == r0 == 1 and H1.shape == H0.shape
     assert np.max(np.abs(H1 - H0)) <= 1e-4 * np.max(np.abs(H0))
