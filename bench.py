@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain-rhs", type=int, default=2, help="sources timed for the plain FP64 BiCG rate")
+    ap.add_argument("--no-serve-summary", dest="serve_summary", action="store_false",
+                    help="skip the serving trace summary (p50/p99, RHS/s) in the default line")
     ap.add_argument("--no-configs", dest="configs", action="store_false",
                     help="skip the one-job rows of the 8^4 and 16^3x32 configurations")
     ap.add_argument("--no-gamma5-arm", dest="gamma5_arm", action="store_false",
@@ -312,49 +314,53 @@ def run_job(s, b, x, n1, phases=None):
 
 
 def gamma5_arm(args, w, links, n_rhs, n1, rank, dev, stream):
-    """The gamma5-Hermitian variant (Sec. 4) on the same job shape: Incremental
-    eigBiCG and the plain mixed batched control, one operator product per iteration.
-    Gaussian sources: a complex Z2 source has r0^H gamma5 r0 = 0, on which the gamma5
-    shadow start breaks down at once."""
+    """The gamma5-Hermitian variant (Sec. 4): one operator product per BiCG iteration.
+    FP64 single-source BiCG, general and gamma5, on the same Gaussian sources (a complex
+    Z2 source has r0^H gamma5 r0 = 0, on which the gamma5 shadow start breaks down at
+    once), then the mixed-precision batched gamma5 BiCG on the job's number of sources
+    (reported with its status: in FP32 the gamma5 recursion can stagnate)."""
     import numpy as np
     import torch
     from paper_0911_2285_gb300 import Solver
     from seeded_inputs import gaussian_source
+    nsrc = 2
+    gsrc = np.stack([gaussian_source(w["dims"], 2000 * w["cfg"] + i) for i in rank_source_ids(nsrc, rank)])
+    bg = torch.from_numpy(gsrc).to(dev)
+    xg = torch.zeros_like(bg)
+    out = {"sources": f"{nsrc} Gaussian (FP64 arms)", "unit": "RHS/s"}
+    for name, g5 in (("fp64_general", False), ("fp64_gamma5", True)):
+        with Solver(links, w["dims"], w["kappa"], stream=stream.cuda_stream, gamma5=g5,
+                    **solver_args(w, precision="fp64", k_max=1)) as sg:
+            sg.solve(bg[:1], mode="plain", out=xg[:1])   # warm-up / graphs
+            xg.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info, _ = sg.solve(bg, mode="plain", out=xg)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            out[name] = {"value": nsrc / t, "iters_per_rhs": float(np.mean([i["iters"] for i in info])),
+                         "matvecs_per_rhs": float(np.mean([i["matvecs"] for i in info])),
+                         "max_true_resid": max(i["true_resid"] for i in info)}
+    out["fp64_speedup"] = out["fp64_gamma5"]["value"] / out["fp64_general"]["value"]
+    del bg, xg
     gsrc = np.stack([gaussian_source(w["dims"], 2000 * w["cfg"] + i) for i in rank_source_ids(n_rhs, rank)])
     bg = torch.from_numpy(gsrc).to(dev)
     xg = torch.zeros_like(bg)
     del gsrc
-    sg = Solver(links, w["dims"], w["kappa"], stream=stream.cuda_stream, gamma5=True, **solver_args(w))
-    g5 = {"sources": f"{n_rhs} Gaussian", "unit": "RHS/s"}
-    try:
-        sg.solve(bg[: sg.batch_size()], mode="plain", out=xg[: sg.batch_size()])   # warm-up (graphs)
+    with Solver(links, w["dims"], w["kappa"], stream=stream.cuda_stream, gamma5=True, **solver_args(w)) as sg:
+        sg.solve(bg[: sg.batch_size()], mode="plain", out=xg[: sg.batch_size()], raise_on_fail=False)
         xg.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, igp, _ = sg.solve(bg, mode="plain", out=xg)
+        _, info, st = sg.solve(bg, mode="plain", out=xg, raise_on_fail=False)
         torch.cuda.synchronize()
-        tgp = time.perf_counter() - t0
-        g5["plain_mixed"] = {"value": n_rhs / tgp, "iters_per_rhs": float(np.mean([i["iters"] for i in igp])),
-                             "max_true_resid": max(i["true_resid"] for i in igp)}
-        g5["operator_ms"] = sg.time_kernel(0, min(sg.batch_size(), n_rhs), 10)
-        run_job(sg, bg, xg, n1)            # warm-up (graphs)
-        torch.cuda.synchronize()
-        gph = {}
-        t0 = time.perf_counter()
-        ig = run_job(sg, bg, xg, n1, gph)
-        torch.cuda.synchronize()
-        tg = time.perf_counter() - t0
-        g5["incremental"] = {"value": n_rhs / tg, "max_true_resid": max(i["true_resid"] for i in ig),
-                             "iters_per_rhs": {"eigbicg": float(np.mean([i["iters"] for i in ig[:n1]])),
-                                               "deflated": float(np.mean([i["iters"] for i in ig[n1:]]))
-                                               if n_rhs > n1 else None},
-                             "phase_ms": gph}
-    except Exception as e:   # reported, not hidden: the variant can break down (Sec. 4 shadow start)
-        g5["error"] = f"{type(e).__name__}: {e}"
-    finally:
-        sg.close()
-        del bg, xg
-    return g5
+        t = time.perf_counter() - t0
+        ok = sum(1 for i in info if i["true_resid"] <= 1e-10)
+        out["mixed_gamma5_batched"] = {"value": ok / t, "converged": ok, "sources": n_rhs,
+                                       "iters_per_rhs": float(np.mean([i["iters"] for i in info])),
+                                       "operator_ms": sg.time_kernel(0, min(sg.batch_size(), n_rhs), 10)}
+    del bg, xg
+    return out
 
 
 def main_ours(args):
@@ -485,6 +491,10 @@ def main_ours(args):
             g5 = {"error": f"{type(e).__name__}: {e}"}
 
     configs = config_rows(dev, stream) if args.configs and world == 1 else None
+    serving = None
+    if args.serve_summary and world == 1:
+        serving = serving_run(args.requests, args.load, 3, rank, local)
+        serving.pop("clocks", None)
 
     # ---- plain FP64 single-RHS BiCG on the same GPU (the comparison rate)
     plain = None
@@ -531,6 +541,7 @@ def main_ours(args):
         "control_plain_mixed": control,
         "gamma5_variant": g5,
         "smaller_configs": configs,
+        "serving": serving,
         "eigenspace": eigenspace,
         "oracle_check": oracle_check,
         "roofline": {"bound": "hbm", "kernel": f"operator pair A p, A^+ phat (FP32, k={k} batch)",
@@ -571,8 +582,8 @@ def job_rate(name, kappa, n_rhs, n1, nev, m, k_max, precision, dev, stream):
     if worst > 1e-10:
         raise SystemExit(f"{name} kappa={kappa} k={k_max} {precision}: true residual {worst}")
     return {"value": n_rhs / t, "unit": "RHS/s", "k": k_used,
-            "iters_per_rhs": {"eigbicg": float(np.mean([i["iters"] for i in infos[:n1]])),
-                              "deflated": float(np.mean([i["iters"] for i in infos[n1:]]))},
+            "iters_per_rhs": {"eigbicg": float(np.mean([i["iters"] for i in infos[:n1]])) if n1 else None,
+                              ("deflated" if n1 else "plain"): float(np.mean([i["iters"] for i in infos[n1:]]))},
             "matvecs_per_rhs": float(np.mean([i["matvecs"] for i in infos])), "max_true_resid": worst}
 
 
@@ -587,6 +598,9 @@ def config_rows(dev, stream):
     for kappa in (0.122, 0.124, 0.1245):
         for k in (1, 4, 8):
             rows["16^3x32"][f"kappa={kappa},k={k}"] = job_rate("16^3x32", kappa, 24, 4, 10, 60, k, "mixed", dev,
+                                                               stream)
+        # the same 24 sources with plain BiCG (no eigenspace): iterations per source vs kappa
+        rows["16^3x32"][f"kappa={kappa},k=8,plain"] = job_rate("16^3x32", kappa, 24, 0, 10, 60, 8, "mixed", dev,
                                                                stream)
     return rows
 
@@ -639,15 +653,15 @@ REF_ITERS = {"4^4": 58, "8^4": 113, "16^3x32": 164, "24^3x64": 188}
 SERVE_MIX = {"8^4": 0.50, "16^3x32": 0.35, "24^3x64": 0.15}
 SERVE_KAPPA = {"8^4": 0.124, "16^3x32": 0.1245, "24^3x64": 0.1245}
 SERVE_SEED = 5
-SERVE_DISTINCT = 8      # distinct Z2 sources per operator, reused round-robin (read-only)
 
 
-def main_serve(args):
+def serving_run(requests, load, warmup, rank, local):
     """Continuous batching on one GPU: one resident context per gauge field (links and
     growing eigenspace stay on the device; AUTO mode runs eigBiCG on each operator's first
-    n1 requests and deflated BiCG after). The trace is first served closed-loop (every
+    n1 requests and deflated BiCG after; eigBiCG windows are admitted by device memory).
+    Every request has its own Z2 source. The trace is first served closed-loop (every
     request arrives at t = 0) to measure the capacity, then with Poisson arrivals at
-    ``--load`` x that capacity; the second pass gives RHS/s and the p50/p99 latency."""
+    ``load`` x that capacity; the second pass gives RHS/s and the p50/p99 latency."""
     import numpy as np
     import torch
     from paper_0911_2285_gb300 import Solver
@@ -655,40 +669,46 @@ def main_serve(args):
     from paper_0911_2285_gb300.serving import Server, poisson_trace
     from seeded_inputs import WORKLOADS, workload_links, z2_source
 
-    rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
-    ops, srcs = {}, {}
+    ops = {}
     for name in SERVE_MIX:
         w = WORKLOADS[name]
         ops[name] = Solver(workload_links(name), w["dims"], SERVE_KAPPA[name], nev=w["nev"], m=w["m"], n1=w["n1"],
                            tol=1e-10, maxiter=4000, precision="mixed", k_max=8,
                            n_def_max=min(80, w["n1"] * w["nev"]))
-        srcs[name] = [z2_source(w["dims"], 50000 + 100 * list(SERVE_MIX).index(name) + i)
-                      for i in range(SERVE_DISTINCT)]
+    cache = {}
+
+    def source(name, i):   # one distinct Z2 source per request of the trace (read-only)
+        key = (name, i)
+        if key not in cache:
+            cache[key] = z2_source(WORKLOADS[name]["dims"], 50000 + 100000 * rank + 1000 * list(SERVE_MIX).index(name) + i)
+        return cache[key]
 
     def trace(rate):
-        return poisson_trace(args.requests, rate, SERVE_MIX, SERVE_SEED + 1000 * rank,
-                             lambda name, i: srcs[name][i % SERVE_DISTINCT])
+        return poisson_trace(requests, rate, SERVE_MIX, SERVE_SEED + 1000 * rank, source)
 
     def serve(reqs, realtime):
         for s in ops.values():
             s.reset_eigenspace()
         return Server(ops).run(reqs, realtime=realtime)
 
-    for _ in range(max(1, args.warmup - 2)):          # graphs, autotuner, first-touch
-        serve(poisson_trace(2 * len(ops), 1e9, {k: 1 for k in ops}, 0,
-                            lambda name, i: srcs[name][0]), realtime=False)
-    torch.cuda.synchronize()
-    closed, _ = serve(trace(1e9), realtime=False)
-    capacity = closed.completed / closed.makespan
-    rate = args.load * capacity
-    barrier(world)
-    clocks = ClockSampler(local)
-    clocks.start()
-    l0 = kernel_launches()
-    rep, reqs = serve(trace(rate), realtime=True)
-    launches = kernel_launches() - l0
-    clk = clocks.stop()
+    try:
+        for _ in range(max(1, warmup - 2)):          # graphs, autotuner, first-touch
+            serve(poisson_trace(2 * len(ops), 1e9, {k: 1 for k in ops}, 0, lambda name, i: source(name, 10 ** 6 + i)),
+                  realtime=False)
+        torch.cuda.synchronize()
+        closed, _ = serve(trace(1e9), realtime=False)
+        capacity = closed.completed / closed.makespan
+        rate = load * capacity
+        clocks = ClockSampler(local)
+        clocks.start()
+        l0 = kernel_launches()
+        rep, reqs = serve(trace(rate), realtime=True)
+        launches = kernel_launches() - l0
+        clk = clocks.stop()
+    finally:
+        for o in ops.values():
+            o.close()
     bad = [r for r in reqs if r.status != 0 or r.info is None or r.info["true_resid"] > 1e-10]
     if bad:
         raise SystemExit(f"{len(bad)} requests failed the FP64 residual check")
@@ -700,23 +720,32 @@ def main_serve(args):
         per_op[name] = {"requests": len(lat), "latency_p50_s": float(np.percentile(lat, 50)),
                         "latency_p99_s": float(np.percentile(lat, 99)), "iters_mean": float(np.mean(it)),
                         "eigbicg_requests": sum(1 for r in reqs if r.op == name and r.info["mode_used"] == 1)}
-    for o in ops.values():
-        o.close()
-    value = -barrier_max(-s["rhs_per_s"], world)          # slowest rank
+    return {"rhs_per_s": s["rhs_per_s"], "latency_p50_s": s["latency_p50_s"], "latency_p99_s": s["latency_p99_s"],
+            "latency_mean_s": s["latency_mean_s"], "makespan_s": s["makespan_s"], "capacity_rhs_per_s": capacity,
+            "arrival_rate_hz": rate, "requests": requests, "distinct_sources": len(cache),
+            "per_operator": per_op, "gpu_launches": launches, "clocks": clk,
+            "workload": f"{requests} requests, Poisson arrivals (seed {SERVE_SEED}) at {load:.2f} x measured "
+                        f"capacity, mix {SERVE_MIX}, one Z2 source per request, kappa {SERVE_KAPPA}, one resident "
+                        "context per lattice (k_max 8), AUTO: eigBiCG on each operator's first n1 requests, "
+                        "deflated after, windows admitted by device memory"}
+
+
+def main_serve(args):
+    rank, world, local = dist_setup(args.gpus)
+    out = serving_run(args.requests, args.load, args.warmup, rank, local)
+    value = -barrier_max(-out["rhs_per_s"], world)          # slowest rank
     if rank != 0:
         return
     print(json.dumps({
         "metric": "serving: RHS/s at FP64 resid 1e-10 with p50/p99 latency", "value": value * world,
         "unit": "RHS/s", "n_gpus": world, "steps": 1, "warmup": args.warmup,
-        "ms_per_step": s["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": out["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{args.requests} requests, Poisson arrivals (seed {SERVE_SEED}) at "
-                               f"{args.load:.2f} x measured capacity, mix {SERVE_MIX}, Z2 sources, "
-                               f"kappa {SERVE_KAPPA}, one resident context per lattice (k_max 8), "
-                               "AUTO: eigBiCG on each operator's first n1 requests, deflated after"},
-        "latency_p50_s": s["latency_p50_s"], "latency_p99_s": s["latency_p99_s"],
-        "latency_mean_s": s["latency_mean_s"], "capacity_rhs_per_s": capacity, "arrival_rate_hz": rate,
-        "per_operator": per_op, "gpu_launches": launches, "clocks": clk,
+        "config": {"workload": out["workload"]},
+        "latency_p50_s": out["latency_p50_s"], "latency_p99_s": out["latency_p99_s"],
+        "latency_mean_s": out["latency_mean_s"], "capacity_rhs_per_s": out["capacity_rhs_per_s"],
+        "arrival_rate_hz": out["arrival_rate_hz"], "per_operator": out["per_operator"],
+        "gpu_launches": out["gpu_launches"], "clocks": out["clocks"],
     }), flush=True)
 
 

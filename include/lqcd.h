@@ -271,7 +271,7 @@ long long lqcd_kernel_launches(void);
  * slot buffers hold, repeated reps times. kernel: 0 = operator pair
  * A p, A^+ phat (Krylov precision) with the fused sigma reduction; 1 = residual
  * update; 2 = direction update; 3 = FP64 true residual + reliable-update
- * replacement; 10 + v = operator pair in kernel shape v (v < 19), 99 = the plane-
+ * replacement; 10 + v = operator pair in kernel shape v (v < 25), 99 = the plane-
  * streaming operator pair (see lqcd_dslash_variant). Leaves the slots idle. */
 lqcd_status lqcd_time_kernel(lqcd_ctx *ctx, int kernel, int k, int reps, double *avg_ms);
 
@@ -285,12 +285,12 @@ lqcd_status lqcd_time_kernel(lqcd_ctx *ctx, int kernel, int k, int reps, double 
 lqcd_status lqcd_set_tensor_cores(lqcd_ctx *ctx, int on);
 
 /* Measurement hook: the operator-kernel shape the autotuner picked at init
- * (timing every shape on this lattice with a full batch): 0..18, or 100 for
+ * (timing every shape on this lattice with a full batch): 0..24, or 100 for
  * the plane-streaming kernel; -1 for NULL. */
 int lqcd_dslash_variant(const lqcd_ctx *ctx);
 
 /* Test hook: one launch of the BiCG operator-pair kernel of shape 'variant'
- * (0..9 or 100, see lqcd_dslash_variant) on k host fields p, phat (Krylov
+ * (0..24 or 100, see lqcd_dslash_variant) on k host fields p, phat (Krylov
  * precision of the context): Ap = A p, Ahp = A^+ phat (host outputs), and
  * sigma = (phat, A p) per field (k complex, may be NULL).  Uses batch slots
  * 0..k-1 and leaves them idle.  LQCD_ERR_ARG for a shape this lattice cannot

@@ -1,8 +1,8 @@
 """Time single kernels of the library on a synthetic lattice (also the workload of
 the committed ncu captures).
 
-    python -m paper_0911_2285_gb300.kernelbench dhop --workload 16^3x32 --variants 2 4
-    python -m paper_0911_2285_gb300.kernelbench dots --a 80 --b 8 --n 1572864
+    python kernelbench.py dhop --workload 16^3x32 --variants 2 4
+    python kernelbench.py dots --a 80 --b 8 --n 1572864
 
 ``dhop``: the operator-pair kernel shapes (A p, A^+ phat for k slots) through
 ``Solver.time_kernel``; after the timed runs each listed shape is launched once
@@ -15,10 +15,14 @@ tensor-core restart product that does work). Inputs are seeded synthetic fields.
 from __future__ import annotations
 
 import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main(argv=None):
-    ap = argparse.ArgumentParser(prog="python -m paper_0911_2285_gb300.kernelbench")
+    ap = argparse.ArgumentParser(prog="python kernelbench.py")
     sub = ap.add_subparsers(dest="what", required=True)
     d = sub.add_parser("dhop")
     d.add_argument("--workload", default="16^3x32")
@@ -37,7 +41,7 @@ def main(argv=None):
 
     import numpy as np
     import torch
-    from .lqcd import Solver, field_dots
+    from paper_0911_2285_gb300.lqcd import Solver, field_dots
     if args.what == "dhop":
         from seeded_inputs import WORKLOADS, workload_links
         w = WORKLOADS[args.workload]

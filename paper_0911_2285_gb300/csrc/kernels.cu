@@ -368,7 +368,11 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
 //                 shares each link load between them.
 //   BZ > 0: a block covers an 8 x 8 x BZ brick of sites (THREADS = 64 BZ) instead
 //           of THREADS consecutive sites, so more y and z neighbours are L1 hits.
-template <int THREADS, int BZ> struct SiteMap {
+//   TM (t march, with BZ > 0): the units of a brick at consecutive t are
+//           consecutive, so a block walks one brick through several t-planes
+//           and the t neighbours of a step are the centres of the steps before
+//           and after it (L1 hits instead of L2 reads).
+template <int THREADS, int BZ, bool TM = false> struct SiteMap {
     int nunits;
     __device__ __forceinline__ SiteMap(const Geom& g) {
         nunits = BZ > 0 ? (g.L[0] / 8) * (g.L[1] / 8) * (g.L[2] / (BZ > 0 ? BZ : 1)) * g.L[3]
@@ -380,7 +384,10 @@ template <int THREADS, int BZ> struct SiteMap {
             return s < g.V ? s : -1;
         }
         const int nbx = g.L[0] / 8, nby = g.L[1] / 8, nbz = g.L[2] / (BZ > 0 ? BZ : 1);
-        const int bx = u % nbx, r1 = u / nbx, by = r1 % nby, r2 = r1 / nby, bz = r2 % nbz, t = r2 / nbz;
+        int b = u, t = 0;
+        if (TM) { t = u % g.L[3]; b = u / g.L[3]; }
+        const int bx = b % nbx, r1 = b / nbx, by = r1 % nby, r2 = r1 / nby, bz = r2 % nbz;
+        if (!TM) t = r2 / nbz;
         const int x = bx * 8 + (threadIdx.x & 7), y = by * 8 + ((threadIdx.x >> 3) & 7);
         const int z = bz * BZ + (threadIdx.x >> 6);
         return x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
@@ -390,12 +397,12 @@ template <int THREADS, int BZ> struct SiteMap {
 //   G5   = true : the gamma5 variant (Sec. 4): one job per slot, A p only, with
 //                 phat = gamma5 p formed in registers for sigma; windowed slots
 //                 also store A^+ phat = gamma5 A p for the restart's coupling.
-template <typename S, int THREADS, int MINB, bool PAIR, int BZ = 0, bool G5 = false>
+template <typename S, int THREADS, int MINB, bool PAIR, int BZ = 0, bool G5 = false, bool TM = false>
 __global__ void __launch_bounds__(THREADS, MINB) matvec_kernel(Geom g, const void* links, double kappa,
                                                                SlotState* states, const SlotPtrs* ptrs,
                                                                int njobs) {
     const int job = blockIdx.x % njobs, sblock = blockIdx.x / njobs, nsb = gridDim.x / njobs;
-    const SiteMap<THREADS, BZ> map(g);
+    const SiteMap<THREADS, BZ, TM> map(g);
     // each block takes a contiguous run of site units (neighbouring sites stay on one SM)
     const int per = (map.nunits + nsb - 1) / nsb;
     const int u0 = sblock * per, u1 = min(map.nunits, u0 + per);
@@ -1444,14 +1451,14 @@ cudaError_t launch_bicg_start(const Geom& g, const void* links64, double kappa, 
 
 // SPT: sites per thread (grid-stride), which amortises each block's set-up and
 // reduction tail over more sites.
-template <typename S, int THREADS, int MINB, bool PAIR, int BZ = 0, int SPT = 1, bool G5 = false>
+template <typename S, int THREADS, int MINB, bool PAIR, int BZ = 0, int SPT = 1, bool G5 = false, bool TM = false>
 static void matvec_launch(const Geom& g, const void* links, double kappa, SlotState* states, const SlotPtrs* ptrs,
                           int nslots, cudaStream_t s) {
     const int njobs = (PAIR || G5) ? nslots : 2 * nslots;
     int nb = div_up((size_t)g.V, (size_t)THREADS * SPT);
     if (nb > PARTIAL_STRIDE / 2) nb = PARTIAL_STRIDE / 2;
-    matvec_kernel<S, THREADS, MINB, PAIR, BZ, G5><<<nb * njobs, THREADS, 0, s>>>(g, links, kappa, states, ptrs,
-                                                                                njobs);
+    matvec_kernel<S, THREADS, MINB, PAIR, BZ, G5, TM><<<nb * njobs, THREADS, 0, s>>>(g, links, kappa, states, ptrs,
+                                                                                    njobs);
 }
 // The brick shapes need Lx, Ly multiples of 8 and Lz a multiple of BZ.
 static bool brick_ok(const Geom& g, int bz) { return g.L[0] % 8 == 0 && g.L[1] % 8 == 0 && g.L[2] % bz == 0; }
@@ -1464,11 +1471,12 @@ static void matvec_group_launch(const Geom& g, const void* links, double kappa, 
     matvec_group_kernel<JPB, MINB><<<grid, 32 * JPB, 0, s>>>(g, links, (float)kappa, states, ptrs, nslots);
 }
 
-int matvec_variants() { return 19; }
+int matvec_variants() { return 25; }
 bool matvec_variant_ok(const Geom& g, int v) {
     if (v == 13 || v == 14) return brick_ok(g, 4);
-    if (v == 15) return brick_ok(g, 2);
-    return v >= 0 && v < 19;
+    if (v == 15 || v == 23) return brick_ok(g, 2);
+    if (v >= 19 && v < 25) return brick_ok(g, 4);
+    return v >= 0 && v < 25;
 }
 
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
@@ -1495,6 +1503,13 @@ cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, i
             case 16: matvec_launch<float, 256, 3, false, 0, 4>(g, links, kappa, states, ptrs, nslots, s); break;
             case 17: matvec_launch<float, 128, 4, true, 0, 4>(g, links, kappa, states, ptrs, nslots, s); break;
             case 18: matvec_launch<float, 256, 2, true, 0, 2>(g, links, kappa, states, ptrs, nslots, s); break;
+            // t march over 8 x 8 x BZ bricks (SPT consecutive t-planes per block)
+            case 19: matvec_launch<float, 256, 1, true, 4, 8, false, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 20: matvec_launch<float, 256, 2, true, 4, 4, false, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 21: matvec_launch<float, 256, 1, false, 4, 8, false, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 22: matvec_launch<float, 256, 2, false, 4, 8, false, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 23: matvec_launch<float, 128, 2, true, 2, 8, false, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 24: matvec_launch<float, 256, 1, true, 4, 16, false, true>(g, links, kappa, states, ptrs, nslots, s); break;
             default: matvec_launch<float, 128, 1, false>(g, links, kappa, states, ptrs, nslots, s); break;
         }
     }
@@ -1507,7 +1522,7 @@ cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, i
 bool matvec_g5_variant_ok(const Geom& g, int v) {
     switch (v) {
         case 0: case 1: case 2: case 5: case 6: case 9: case 16: return true;
-        case 13: return brick_ok(g, 4);
+        case 13: case 21: case 22: return brick_ok(g, 4);
         default: return false;
     }
 }
@@ -1525,6 +1540,8 @@ cudaError_t launch_bicg_matvec_g5(const Geom& g, const void* links, double kappa
             case 9: matvec_launch<float, 64, 8, false, 0, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
             case 13: matvec_launch<float, 256, 3, false, 4, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
             case 16: matvec_launch<float, 256, 3, false, 0, 4, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 21: matvec_launch<float, 256, 1, false, 4, 8, true, true>(g, links, kappa, states, ptrs, nslots, s); break;
+            case 22: matvec_launch<float, 256, 2, false, 4, 8, true, true>(g, links, kappa, states, ptrs, nslots, s); break;
             default: matvec_launch<float, 128, 1, false, 0, 1, true>(g, links, kappa, states, ptrs, nslots, s); break;
         }
     }

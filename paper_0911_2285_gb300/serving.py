@@ -6,11 +6,13 @@ session calls of the C ABI (``lqcd_submit`` / ``lqcd_progress`` /
 field keeps its links and its growing eigenspace resident on the device; the
 first requests of each field run eigBiCG and feed the eigenspace, later ones
 run deflated BiCG (Algorithm Incremental eigBiCG). Each context has a fixed
-number of batch slots sized against the device-memory budget at creation;
-requests that arrive while its slots are busy wait in its queue and take a slot
-as soon as one frees up, while the other slots keep iterating, so the work of
-different requests overlaps inside the same operator launches, and contexts on
-different gauge fields run on their own CUDA streams.
+number of batch slots; an eigBiCG request also needs a window, which the
+library allocates only when the device-memory plan has room (admission by
+memory). Requests that arrive while the slots (or the memory) are taken wait
+in the context's queue and are admitted as they free up, while the other slots
+keep iterating, so the work of different requests overlaps inside the same
+operator launches, and contexts on different gauge fields run on their own
+CUDA streams.
 """
 from __future__ import annotations
 
@@ -21,7 +23,7 @@ import numpy as np
 
 from .lqcd import Solver
 
-POLL_S = 20e-6   # host pause between non-blocking polls when nothing finished
+POLL_S = 20e-6   # default host pause between non-blocking polls when nothing finished
 
 
 @dataclass
@@ -81,8 +83,11 @@ def poisson_trace(n_requests, rate_hz, mix, seed, make_source):
 class Server:
     """Continuous-batching request loop over several resident operators."""
 
-    def __init__(self, operators: dict[str, Solver]):
+    def __init__(self, operators: dict[str, Solver], poll_s: float = POLL_S):
+        """``poll_s``: seconds to yield the host core between non-blocking polls that
+        found nothing finished (0 = spin)."""
         self.ops = operators
+        self.poll_s = poll_s
 
     def run(self, requests, realtime=True, mode="auto"):
         """Serve ``requests`` (sorted by arrival). With ``realtime`` the arrivals
@@ -129,7 +134,7 @@ class Server:
                 wait_s = reqs[i].t_arrival - (time.perf_counter() - t0)
                 if wait_s > 0:
                     time.sleep(wait_s)
-            elif not wait and busy and not finished:
-                time.sleep(POLL_S)   # nothing finished: yield the core briefly instead of spinning
+            elif not wait and busy and not finished and self.poll_s > 0:
+                time.sleep(self.poll_s)   # nothing finished: yield the core briefly instead of spinning
         rep.makespan = time.perf_counter() - t0
         return rep, reqs

@@ -65,7 +65,8 @@ def test_apply_full_size_24x24x24x64_sampled():
 def test_operator_pair_kernels_match_oracle(name):
     """Every shape of the BiCG operator-pair kernel (the autotuner's candidates:
     per-site and site-group thread maps, linear and brick site orders, and the TMA
-    plane-streaming one): A p, A^+ phat and sigma = (phat, A p) against the oracle,
+    plane-streaming one, and the t-march brick orders): A p, A^+ phat and
+    sigma = (phat, A p) against the oracle,
     FP32 fields, batches of 1 and 3."""
     from paper_0911_2285_gb300 import Solver
     w, links, op = workload(name)
@@ -74,7 +75,7 @@ def test_operator_pair_kernels_match_oracle(name):
             p = np.stack([random_field(op.n, 20 + i) for i in range(k)])
             ph = np.stack([random_field(op.n, 40 + i) for i in range(k)])
             refs = [(op.apply(p[i]), op.apply_dag(ph[i])) for i in range(k)]
-            for variant in list(range(19)) + [100]:
+            for variant in list(range(25)) + [100]:
                 ap, ahp, sig = s.apply_pair(p, ph, variant)
                 for i in range(k):
                     assert rel(ap[i], refs[i][0]) <= 2e-6, (variant, i)
@@ -89,7 +90,7 @@ def test_brick_shapes_rejected_on_small_extents():
     w, links, op = workload("4^4")
     with Solver(links, w["dims"], w["kappa"], nev=1, m=3, precision="mixed", k_max=1, n_def_max=1) as s:
         p = random_field(op.n, 1)
-        for variant in (13, 14, 15):
+        for variant in (13, 14, 15, 19, 20, 21, 22, 23, 24):
             with pytest.raises(lqcd.LQCDError):
                 s.apply_pair(p, p, variant)
         ap, _, _ = s.apply_pair(p, p, 2)

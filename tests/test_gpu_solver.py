@@ -115,14 +115,16 @@ def test_eigbicg_free_field_ritz_closed_form_on_gpu():
             # FP64 Rayleigh-Ritz on the stored eigenspace (Sec. 2): two-sided accuracy
             ev, res, _, _ = s.eigs()
             best = ev[np.argmin(np.abs(ev - exact))]
-            # FP32 Krylov vectors (MIXED): the window's quality depends on rounding
-            # (1e-4 .. 3e-2 eigen-residuals here, with the operator shape the autotuner
-            # picks); the two-sided Rayleigh-Ritz error stays below the eigen-residual
+            # MIXED: the lowest free-field eigenvalue is 12-fold degenerate and a
+            # single source's Krylov space holds one vector of it; FP32 rounding
+            # excites the other eleven directions, which the window (nev = 4) cannot
+            # hold apart, so the error depends on the rounding of the operator shape
+            # the autotuner picks (1.2e-6 .. 3.6e-4 measured). The fixed 1e-6 bound
+            # on a non-degenerate spectrum is in test_gpu_eigenspace.py.
             if prec == "fp64":
                 assert abs(best - exact) <= 1e-10 * exact, ev
             else:
-                rb = res[np.argmin(np.abs(ev - exact))]
-                assert abs(best - exact) <= max(1e-4, rb) * exact, (ev, res)
+                assert abs(best - exact) <= 1e-3 * exact, (ev, res)
 
 
 def test_deflate_matches_oracle():
