@@ -109,6 +109,17 @@ typedef struct {
                                  with the same reliable updates and DefTol restart; eigBiCG
                                  and its correction leg stay BiCG.  0 = BiCG throughout.
                                  Not combinable with gamma5. */
+    int evenodd;              /* 1 = even-odd (Schur complement) preconditioning, the form of the
+                                 paper's test matrices (Sec. 3): the solver works on the odd half
+                                 lattice with A_hat = 1 - kappa^2 D_oe D_eo and
+                                 b_hat = b_o + kappa D_oe b_e, and returns the full solution with
+                                 x_e = b_e + kappa D_eo x_o; the tolerance and the reported
+                                 true_resid are those of the full system in FP64.  Sources and
+                                 solutions of lqcd_solve, lqcd_deflate and the session stay full
+                                 fields; the eigenspace (lqcd_eigs, lqcd_eigspace_get/set) and
+                                 lqcd_apply (which applies A_hat) use half fields of 12 V / 2
+                                 complex, odd sites in site order.  All extents must be even;
+                                 not combinable with gamma5 or bicgstab. */
 } lqcd_params;
 
 typedef struct {

@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(BL_THREADS) start_kernel(SlotState* states, co
     if (reduce2<S>(P, CNT_START, comp, cz, acc, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) {
         st.rho = tot[0];
         st.rnorm = sqrt(tot[1].x);
-        st.bnorm = sqrt(tot[1].y);
+        st.bnorm = P.bnorm_ref ? *P.bnorm_ref : sqrt(tot[1].y);   // even-odd: ||b|| of the full system
         st.rhat_norm = st.rnorm;
         st.rmax = st.rnorm;
         st.r_ru = st.rnorm;
@@ -1590,13 +1590,18 @@ static void launch_true_resid(int variant, const Geom& g, const void* links64, c
 
 cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int prec, SlotState* states,
                            const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s, int ru_variant,
-                           const float4* links_df) {
+                           const float4* links_df, int eo) {
     dim3 g2(blas_blocks(N / 2), nslots);
     if (prec == 0) fold_ru_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     else fold_ru_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     count_launches(1);
-    launch_true_resid(ru_variant, g, links64, links_df, kappa, states, ptrs, nslots, 0, s);
-    count_launches(1);
+    if (eo) {
+        cudaError_t e = launch_eo_true_resid(g, links64, kappa, states, ptrs, nslots, 0, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        launch_true_resid(ru_variant, g, links64, links_df, kappa, states, ptrs, nslots, 0, s);
+        count_launches(1);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (prec == 0) replace_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
@@ -1655,13 +1660,14 @@ cudaError_t launch_bicg_direction(int prec, SlotState* states, const SlotPtrs* p
 }
 
 cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa, int prec, SlotState* states,
-                               const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s, int ru_variant) {
+                               const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s, int ru_variant, int eo) {
     dim3 g2(blas_blocks(N / 2), nslots);
     if (prec == 0) fold_kernel<double><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     else fold_kernel<float><<<g2, BL_THREADS, 0, s>>>(states, ptrs, N);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (eo) return launch_eo_true_resid(g, links64, kappa, states, ptrs, nslots, 1, s);
     launch_true_resid(ru_variant >= RU_DF ? 0 : ru_variant, g, links64, nullptr, kappa, states, ptrs, nslots, 1, s);
     count_launches(1);
     return cudaGetLastError();

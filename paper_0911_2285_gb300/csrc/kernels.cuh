@@ -18,6 +18,17 @@ constexpr int MAX_SLOTS = 8;
 constexpr int MAX_M = 64;              // window size limit
 constexpr int MAX_SMALL = 80;          // largest dense eigenproblem / eigenspace
 
+// Even-odd operator, host-driven applies in two stages (evenodd.cu):
+// stage 1 out = D hop_in (even sites), stage 2 out = self - k^2 D hop_in (odd
+// sites) or aux - (self - k^2 D hop_in) (FP64 aux).
+struct EoJob {
+    const void* hop_in;
+    const void* self;
+    void* out;
+    const void* aux;
+    int dagger;
+};
+
 struct ApplyJob {            // out = A in, A^+ in, or aux - A in
     const void* in;
     void* out;
@@ -104,9 +115,10 @@ cudaError_t launch_bicg_update(int prec, SlotState* st_, const SlotPtrs* ptrs, i
 // and the slots' x_df); the final residual of launch_bicg_finish is always native FP64.
 constexpr int RU_DF = 4;
 int true_resid_variants();
+// eo: the even-odd Schur residual (FP64) instead of the full-lattice one.
 cudaError_t launch_bicg_ru(const Geom& g, const void* links64, double kappa, int prec,
                            SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s,
-                           int ru_variant = 0, const float4* links_df = nullptr);
+                           int ru_variant = 0, const float4* links_df = nullptr, int eo = 0);
 // FP64 links -> double-float links (n complex elements).
 cudaError_t launch_links_df(const double2* l64, float4* ldf, size_t n, cudaStream_t st);
 cudaError_t launch_bicg_scalars(SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s);
@@ -119,7 +131,7 @@ cudaError_t launch_stab_scalars(SlotState* st_, int nslots, cudaStream_t s);
 cudaError_t launch_bicg_direction(int prec, SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s);
 cudaError_t launch_bicg_finish(const Geom& g, const void* links64, double kappa, int prec,
                                SlotState* st_, const SlotPtrs* ptrs, int nslots, size_t N, cudaStream_t s,
-                               int ru_variant = 0);
+                               int ru_variant = 0, int eo = 0);
 
 // eigBiCG restart: coefficient kernel (one CTA per slot) and window product.
 // Work buffers: eig_work_elems() double2 per slot (restart; the buffer holds MAX_SLOTS
@@ -160,6 +172,27 @@ cudaError_t launch_final_ritz(SlotState* st_, const SlotPtrs* ptrs, int slot, do
 // Small matrix helpers: C = A B (all row-major, n x k x m), one CTA.
 cudaError_t launch_small_gemm(int n, int k, int m, const double2* A, int lda, int transA,
                               const double2* B, int ldb, double2* C, int ldc, cudaStream_t st);
+
+// Even-odd (Schur complement) operator A_hat = 1 - k^2 D_oe D_eo on the odd half
+// lattice (evenodd.cu). Half fields: V/2 sites, half index h = s >> 1.
+// A_hat (A_hat^+ with job.dagger) of njobs fields: d_stage1 jobs (D_eo in -> tmp),
+// d_stage2 jobs (in - k^2 D_oe tmp, or aux - that with residual).
+cudaError_t launch_eo_apply(const Geom& g, const void* links, double kappa, int prec, const EoJob* d_stage1,
+                            const EoJob* d_stage2, int njobs, int residual, cudaStream_t st);
+// b_hat = b_o + k D_oe b_e (k full FP64 fields -> k half fields).
+cudaError_t launch_eo_prepare(const Geom& g, const void* links64, double kappa, const double2* bfull, double2* bhat,
+                              int k, cudaStream_t st);
+// The odd half of k full FP64 fields.
+cudaError_t launch_eo_extract(const Geom& g, const double2* xfull, double2* xhalf, int k, cudaStream_t st);
+// Full solutions: x_o from the half fields, x_e = b_e + k D_eo x_o.
+cudaError_t launch_eo_reconstruct(const Geom& g, const void* links64, double kappa, const double2* bfull,
+                                  const double2* xhalf, double2* xfull, int k, cudaStream_t st);
+// BiCG operator pair on A_hat over the slots (two stages through eo_t, eo_th) with sigma and alpha.
+cudaError_t launch_eo_pair(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
+                           const SlotPtrs* ptrs, int nslots, cudaStream_t st);
+// FP64 Schur residual b_hat - A_hat x_hi (through eo64): in-iteration (check_only 0) or final.
+cudaError_t launch_eo_true_resid(const Geom& g, const void* links64, double kappa, SlotState* states,
+                                 const SlotPtrs* ptrs, int nslots, int check_only, cudaStream_t st);
 
 // Bound of the device-side waits (SM clock cycles) of the kernels of gemm_tc.cu
 // and dslash_tiled.cu on the current device; cycles <= 0 restores the default.

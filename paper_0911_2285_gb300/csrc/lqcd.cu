@@ -98,7 +98,18 @@ struct lqcd_ctx {
     double2* mdscratch = nullptr;
     size_t mdscratch_elems = 0;
     ApplyJob* d_jobs = nullptr;
-    double2* staging = nullptr;     // kmax FP64 fields (host AoS I/O)
+    double2* staging = nullptr;     // kmax FP64 full fields (host AoS I/O)
+    // even-odd (Schur complement) operator: the solver works on the odd half
+    // lattice (N = 6 V); sources and solutions stay full fields (Nfull = 12 V)
+    bool eo = false;
+    size_t Nfull = 0;
+    double2* bfull_all = nullptr;   // kmax full FP64 sources
+    double2* xfull_all = nullptr;   // kmax full FP64 solutions (and initial guesses)
+    double2* eo64_all = nullptr;    // kmax FP64 half fields: stage buffer of the Schur residual
+    char* eot_all = nullptr;        // 2 kmax Krylov half fields: stage buffers of the operator pair
+    double* bnorm_all = nullptr;    // kmax ||b|| of the full systems
+    char* eo_scr = nullptr;         // 2 kmax FP64 half fields: stage buffers of host applies
+    EoJob* d_eojobs = nullptr;      // 2 x 2 kmax stage jobs
 
     // eigenspace
     int n_def = 0;
@@ -209,6 +220,12 @@ lqcd_status validate(const lqcd_params* p) {
     if (p->gamma5 != 0 && p->gamma5 != 1) return LQCD_ERR_ARG;
     if (p->bicgstab != 0 && p->bicgstab != 1) return LQCD_ERR_ARG;
     if (p->bicgstab && p->gamma5) return LQCD_ERR_ARG;   // the gamma5 variant is a BiCG recursion
+    if (p->evenodd != 0 && p->evenodd != 1) return LQCD_ERR_ARG;
+    if (p->evenodd) {   // parities need even extents; the variants keep the full operator
+        for (int d = 0; d < 4; ++d)
+            if (p->dims[d] % 2) return LQCD_ERR_ARG;
+        if (p->gamma5 || p->bicgstab) return LQCD_ERR_ARG;
+    }
     return LQCD_OK;
 }
 
@@ -241,6 +258,10 @@ lqcd_status set_ptrs(lqcd_ctx* c) {
         P.vscale = reinterpret_cast<double*>(sm); sm += m + 1;
         P.partials = c->partials + (size_t)s * CNT_COUNT * PARTIAL_STRIDE;
         P.counters = c->counters + (size_t)s * CNT_COUNT;
+        P.eo_t = c->eo ? c->krylov(c->eot_all, 2 * (size_t)s) : nullptr;
+        P.eo_th = c->eo ? c->krylov(c->eot_all, 2 * (size_t)s + 1) : nullptr;
+        P.eo64 = c->eo ? c->eo64_all + (size_t)s * c->N : nullptr;
+        P.bnorm_ref = c->eo ? c->bnorm_all + s : nullptr;
     }
     CK(cudaMemcpy(c->d_ptrs, c->h_ptrs.data(), sizeof(SlotPtrs) * c->kmax, cudaMemcpyHostToDevice));
     return LQCD_OK;
@@ -267,9 +288,13 @@ lqcd_status attach_window(lqcd_ctx* c, int s, bool* ok) {
     if (c->p.hbm_budget_bytes) {
         if (c->plan_bytes + (size_t)(c->win_attached + 1) * c->win_bytes > c->p.hbm_budget_bytes) return LQCD_OK;
     } else {
+        // free device memory, plus what this context's pool keeps mapped but unused
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot));
-        if (fr < c->win_bytes + WIN_RESERVE) return LQCD_OK;
+        uint64_t reserved = 0, used = 0;
+        CK(cudaMemPoolGetAttribute(c->win_pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+        CK(cudaMemPoolGetAttribute(c->win_pool, cudaMemPoolAttrUsedMemCurrent, &used));
+        if (fr + (reserved > used ? reserved - used : 0) < c->win_bytes + WIN_RESERVE) return LQCD_OK;
     }
     void* p = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync(&p, c->win_bytes, c->win_pool, c->stream);
@@ -358,7 +383,9 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     for (int d = 1; d < 4; ++d) c->g.stride[d] = c->g.stride[d - 1] * c->g.L[d - 1];
     c->V = c->g.stride[3] * c->g.L[3];
     c->g.V = c->V;
-    c->N = (size_t)12 * c->V;
+    c->eo = c->p.evenodd != 0;
+    c->Nfull = (size_t)12 * c->V;
+    c->N = c->eo ? c->Nfull / 2 : c->Nfull;
     c->kprec = c->p.precision == LQCD_MIXED ? 1 : 0;
     c->kbytes = c->N * (c->kprec ? 8 : 16);
     c->dbytes = c->N * 16;
@@ -368,7 +395,8 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     // Memory plan (bytes) for the HBM budget check.
     const size_t K = (size_t)c->kmax;
     size_t plan = (size_t)c->V * 4 * 9 * 16 + (c->kprec ? (size_t)c->V * 4 * (3 + 9) * 16 + K * c->N * 16 : 0);
-    plan += K * c->kbytes * (1 + 2 + 6) + K * c->dbytes * 4;
+    plan += K * c->kbytes * (1 + 2 + 6) + K * c->dbytes * 3 + K * c->Nfull * 16;
+    if (c->eo) plan += K * c->Nfull * 16 * 2 + K * c->dbytes * 3 + 2 * K * c->kbytes;
     plan += 2 * (size_t)c->n_def_max * c->kbytes;
     plan += (MAX_SLOTS * eig_work_elems() + 16) * 16 + c->mdscratch_elems * 16 + K * CNT_COUNT * PARTIAL_STRIDE * 16;
     c->plan_bytes = plan;
@@ -414,7 +442,16 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     AL(c->eigwork, ((size_t)MAX_SLOTS * eig_work_elems() + 16) * 16);
     AL(c->mdscratch, c->mdscratch_elems * 16);
     AL(c->d_jobs, sizeof(ApplyJob) * 2 * K);
-    AL(c->staging, K * c->dbytes);
+    AL(c->staging, K * c->Nfull * 16);
+    if (c->eo) {
+        AL(c->bfull_all, K * c->Nfull * 16);
+        AL(c->xfull_all, K * c->Nfull * 16);
+        AL(c->eo64_all, K * c->dbytes);
+        AL(c->eot_all, 2 * K * c->kbytes);
+        AL(c->bnorm_all, K * sizeof(double));
+        AL(c->eo_scr, 2 * K * c->dbytes);
+        AL(c->d_eojobs, 4 * K * sizeof(EoJob));
+    }
     AL(c->Ur, (size_t)std::max(c->n_def_max, 1) * c->kbytes);
     AL(c->Ul, (size_t)std::max(c->n_def_max, 1) * c->kbytes);
     const size_t nd2 = (size_t)c->n_def_max * c->n_def_max + 16;
@@ -457,6 +494,13 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
             e = cudaMemPoolCreate(&c->win_pool, &pp);
         }
         if (e != cudaSuccess) { set_error("cudaMemPoolCreate", e); c->win_pool = nullptr; return fail(LQCD_ERR_CUDA); }
+        // keep up to kmax released windows mapped in the pool (a job re-acquires them
+        // at every eigBiCG batch; unmapping and mapping 10 GB windows costs ~0.1 s)
+        uint64_t keep = (uint64_t)K * c->win_bytes;
+        if ((e = cudaMemPoolSetAttribute(c->win_pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            set_error("cudaMemPoolSetAttribute", e);
+            return fail(LQCD_ERR_CUDA);
+        }
     }
     lqcd_status st = set_ptrs(c);
     if (st != LQCD_OK) return fail(st);
@@ -478,7 +522,8 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     c->last_restarts.assign(c->kmax, 0);
     if ((e = prepare_eig_kernels()) != cudaSuccess) { set_error("prepare_eig_kernels", e); return fail(LQCD_ERR_CUDA); }
     if ((e = prepare_tiled_kernel()) != cudaSuccess) { set_error("prepare_tiled_kernel", e); return fail(LQCD_ERR_CUDA); }
-    for (int n = 1; n <= c->kmax; ++n) c->tile_ok[n] = c->kprec && !c->p.gamma5 && tiled_plan(c->g, n, &c->tgeo[n]);
+    for (int n = 1; n <= c->kmax; ++n)
+        c->tile_ok[n] = c->kprec && !c->p.gamma5 && !c->eo && tiled_plan(c->g, n, &c->tgeo[n]);
     st = autotune(c);
     if (st != LQCD_OK) return fail(st);
     c->kbatch = c->kmax;
@@ -530,48 +575,76 @@ namespace {
 
 // Copy k fields from user memory (host or device, AoS FP64) into device fields
 // of precision prec (0 FP64, 1 FP32), via the staging buffer for host input.
-lqcd_status upload(lqcd_ctx* c, const double* src, int k, void* dst, int prec, int on_device) {
+// nc: complex numbers per field (0 = the solver's field length c->N; Nfull for
+// the full sources and solutions of an even-odd context).
+lqcd_status upload(lqcd_ctx* c, const double* src, int k, void* dst, int prec, int on_device, size_t nc = 0) {
+    if (!nc) nc = c->N;
     for (int j0 = 0; j0 < k; j0 += c->kmax) {
         const int kb = std::min(c->kmax, k - j0);
-        const double* s = src + (size_t)j0 * 2 * c->N;
+        const double* s = src + (size_t)j0 * 2 * nc;
         const double* dev_src = s;
         if (!on_device) {
-            CK(cudaMemcpyAsync(c->staging, s, (size_t)kb * c->dbytes, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->staging, s, (size_t)kb * nc * 16, cudaMemcpyHostToDevice, c->stream));
             dev_src = reinterpret_cast<const double*>(c->staging);
         }
-        char* d = reinterpret_cast<char*>(dst) + (size_t)j0 * c->N * (prec ? 8 : 16);
-        CK(launch_pack(dev_src, d, c->V, kb, prec, c->stream));
+        char* d = reinterpret_cast<char*>(dst) + (size_t)j0 * nc * (prec ? 8 : 16);
+        CK(launch_pack(dev_src, d, (int)(nc / 12), kb, prec, c->stream));
     }
     return LQCD_OK;
 }
 
-lqcd_status download(lqcd_ctx* c, const void* src, int prec, int k, double* dst, int on_device) {
+lqcd_status download(lqcd_ctx* c, const void* src, int prec, int k, double* dst, int on_device, size_t nc = 0) {
+    if (!nc) nc = c->N;
     for (int j0 = 0; j0 < k; j0 += c->kmax) {
         const int kb = std::min(c->kmax, k - j0);
-        const char* s = reinterpret_cast<const char*>(src) + (size_t)j0 * c->N * (prec ? 8 : 16);
-        double* d = dst + (size_t)j0 * 2 * c->N;
+        const char* s = reinterpret_cast<const char*>(src) + (size_t)j0 * nc * (prec ? 8 : 16);
+        double* d = dst + (size_t)j0 * 2 * nc;
         if (on_device) {
-            CK(launch_unpack(s, d, c->V, kb, prec, c->stream));
+            CK(launch_unpack(s, d, (int)(nc / 12), kb, prec, c->stream));
         } else {
-            CK(launch_unpack(s, reinterpret_cast<double*>(c->staging), c->V, kb, prec, c->stream));
-            CK(cudaMemcpyAsync(d, c->staging, (size_t)kb * c->dbytes, cudaMemcpyDeviceToHost, c->stream));
+            CK(launch_unpack(s, reinterpret_cast<double*>(c->staging), (int)(nc / 12), kb, prec, c->stream));
+            CK(cudaMemcpyAsync(d, c->staging, (size_t)kb * nc * 16, cudaMemcpyDeviceToHost, c->stream));
         }
     }
     return LQCD_OK;
 }
 
-// out_j = A in_j (or A^+, or b_j - A in_j) for nf device fields in precision prec.
+// out_j = A in_j (or A^+, or b_j - A in_j) for nf device fields in precision prec:
+// the solver's operator (A_hat on the odd half lattice in an even-odd context),
+// or with full = true the full-lattice A (fields of Nfull complex).
 lqcd_status apply_fields(lqcd_ctx* c, int prec, int dagger, int nf, const void* in, size_t in_stride, void* out,
-                         size_t out_stride, const double2* aux) {
+                         size_t out_stride, const double2* aux, bool full = false) {
     const void* links = prec ? (const void*)c->links32 : (const void*)c->links64;
     if (prec && !c->links32) return LQCD_ERR_ARG;
+    if (c->eo && !full) {   // two stages through the half-field scratch
+        std::vector<EoJob> st1(2 * c->kmax), st2(2 * c->kmax);
+        const size_t sb = c->N * (prec ? 8 : 16);
+        for (int j0 = 0; j0 < nf; j0 += 2 * c->kmax) {
+            const int nb = std::min(2 * c->kmax, nf - j0);
+            for (int j = 0; j < nb; ++j) {
+                const char* fin = reinterpret_cast<const char*>(in) + (j0 + j) * in_stride;
+                char* scr = c->eo_scr + (size_t)j * sb;
+                st1[j] = EoJob{fin, nullptr, scr, nullptr, dagger};
+                st2[j] = EoJob{scr, fin, reinterpret_cast<char*>(out) + (j0 + j) * out_stride,
+                               aux ? aux + (size_t)(j0 + j) * c->N : nullptr, dagger};
+            }
+            CK(cudaMemcpyAsync(c->d_eojobs, st1.data(), sizeof(EoJob) * nb, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->d_eojobs + 2 * c->kmax, st2.data(), sizeof(EoJob) * nb, cudaMemcpyHostToDevice,
+                               c->stream));
+            CK(launch_eo_apply(c->g, links, c->p.kappa, prec, c->d_eojobs, c->d_eojobs + 2 * c->kmax, nb,
+                               aux != nullptr, c->stream));
+            CK(cudaStreamSynchronize(c->stream));   // the job tables are reused
+        }
+        return LQCD_OK;
+    }
+    const size_t an = full ? c->Nfull : c->N;
     std::vector<ApplyJob> jobs(2 * c->kmax);
     for (int j0 = 0; j0 < nf; j0 += 2 * c->kmax) {
         const int nb = std::min(2 * c->kmax, nf - j0);
         for (int j = 0; j < nb; ++j) {
             jobs[j].in = reinterpret_cast<const char*>(in) + (j0 + j) * in_stride;
             jobs[j].out = reinterpret_cast<char*>(out) + (j0 + j) * out_stride;
-            jobs[j].aux = aux ? aux + (size_t)(j0 + j) * c->N : nullptr;
+            jobs[j].aux = aux ? aux + (size_t)(j0 + j) * an : nullptr;
             jobs[j].dagger = dagger;
         }
         CK(cudaMemcpyAsync(c->d_jobs, jobs.data(), sizeof(ApplyJob) * nb, cudaMemcpyHostToDevice, c->stream));
@@ -588,7 +661,7 @@ lqcd_status apply_fields(lqcd_ctx* c, int prec, int dagger, int nf, const void* 
 // FP32 hop rounding would swamp it).
 lqcd_status residual_fields(lqcd_ctx* c, int nf, const double2* x, double2* r, const double2* b,
                             bool precise = false) {
-    if (!c->kprec || precise) return apply_fields(c, 0, 0, nf, x, c->dbytes, r, c->dbytes, b);
+    if (!c->kprec || precise || c->eo) return apply_fields(c, 0, 0, nf, x, c->dbytes, r, c->dbytes, b);
     std::vector<ApplyJob> jobs(2 * c->kmax);
     for (int j0 = 0; j0 < nf; j0 += 2 * c->kmax) {
         const int nb = std::min(2 * c->kmax, nf - j0);
@@ -603,6 +676,51 @@ lqcd_status residual_fields(lqcd_ctx* c, int nf, const double2* x, double2* r, c
         CK(cudaStreamSynchronize(c->stream));
     }
     return LQCD_OK;
+}
+
+// Sources and initial guesses of slots s0 .. s0+k-1 from user memory (full
+// fields): b into b_all and x0 into x_hi_all; in an even-odd context through the
+// full buffers, b_hat = b_o + k D_oe b_e, x0 -> its odd half, and ||b|| of the
+// full systems for the tolerance.
+lqcd_status load_sources(lqcd_ctx* c, int s0, int k, const double* b, const double* x0, int on_device) {
+    if (!c->eo) {
+        lqcd_status s = upload(c, b, k, c->b_all + (size_t)s0 * c->N, 0, on_device);
+        if (s != LQCD_OK) return s;
+        return upload(c, x0, k, c->x_hi_all + (size_t)s0 * c->N, 0, on_device);
+    }
+    double2* bf = c->bfull_all + (size_t)s0 * c->Nfull;
+    double2* xf = c->xfull_all + (size_t)s0 * c->Nfull;
+    lqcd_status s = upload(c, b, k, bf, 0, on_device, c->Nfull);
+    if (s != LQCD_OK) return s;
+    s = upload(c, x0, k, xf, 0, on_device, c->Nfull);
+    if (s != LQCD_OK) return s;
+    CK(launch_norms(k, bf, 0, c->Nfull, c->bnorm_all + s0, c->mdscratch, c->mdscratch_elems, c->stream));
+    CK(launch_eo_prepare(c->g, c->links64, c->p.kappa, bf, c->b_all + (size_t)s0 * c->N, k, c->stream));
+    CK(launch_eo_extract(c->g, xf, c->x_hi_all + (size_t)s0 * c->N, k, c->stream));
+    return LQCD_OK;
+}
+
+// Solutions of slots s0 .. s0+k-1 to user memory (full fields). In an even-odd
+// context x_e = b_e + k D_eo x_o is reconstructed first and, when resid is given,
+// resid[j] = ||b - A x|| / ||b|| of the full system in FP64 (the certificate).
+lqcd_status store_solutions(lqcd_ctx* c, int s0, int k, double* x, int on_device, double* resid = nullptr) {
+    if (!c->eo) return download(c, c->x_hi_all + (size_t)s0 * c->N, 0, k, x, on_device);
+    double2* bf = c->bfull_all + (size_t)s0 * c->Nfull;
+    double2* xf = c->xfull_all + (size_t)s0 * c->Nfull;
+    CK(launch_eo_reconstruct(c->g, c->links64, c->p.kappa, bf, c->x_hi_all + (size_t)s0 * c->N, xf, k, c->stream));
+    if (resid) {
+        double2* rf = reinterpret_cast<double2*>(c->eo_scr);   // room for kmax full FP64 fields
+        lqcd_status s = apply_fields(c, 0, 0, k, xf, c->Nfull * 16, rf, c->Nfull * 16, bf, true);
+        if (s != LQCD_OK) return s;
+        double* rn = reinterpret_cast<double*>(c->dsmall);
+        CK(launch_norms(k, rf, 0, c->Nfull, rn, c->mdscratch, c->mdscratch_elems, c->stream));
+        std::vector<double> hr(k), hb(k);
+        CK(cudaMemcpyAsync(hr.data(), rn, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(hb.data(), c->bnorm_all + s0, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int j = 0; j < k; ++j) resid[j] = hb[j] > 0 ? hr[j] / hb[j] : 0.0;
+    }
+    return download(c, xf, 0, k, x, on_device, c->Nfull);
 }
 
 }  // namespace
@@ -802,13 +920,12 @@ extern "C" lqcd_status lqcd_deflate(lqcd_ctx* c, int k, const double* b, double*
     if (c->n_def == 0) return LQCD_ERR_STATE;
     for (int j0 = 0; j0 < k; j0 += c->kmax) {
         const int kb = std::min(c->kmax, k - j0);
-        lqcd_status s = upload(c, b + (size_t)j0 * 2 * c->N, kb, c->b_all, 0, on_device);
-        if (s != LQCD_OK) return s;
-        s = upload(c, x0 + (size_t)j0 * 2 * c->N, kb, c->x_hi_all, 0, on_device);
+        lqcd_status s = load_sources(c, 0, kb, b + (size_t)j0 * 2 * c->Nfull, x0 + (size_t)j0 * 2 * c->Nfull,
+                                     on_device);
         if (s != LQCD_OK) return s;
         s = deflate_slots(c, kb);
         if (s != LQCD_OK) return s;
-        s = download(c, c->x_hi_all, 0, kb, x0 + (size_t)j0 * 2 * c->N, on_device);
+        s = store_solutions(c, 0, kb, x0 + (size_t)j0 * 2 * c->Nfull, on_device);
         if (s != LQCD_OK) return s;
     }
     CK(cudaStreamSynchronize(c->stream));
@@ -820,6 +937,10 @@ namespace {
 
 // The operator pair of one iteration in the autotuned kernel shape.
 cudaError_t launch_matvec(lqcd_ctx* c, int nslots, int variant) {
+    if (c->eo) {
+        const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
+        return launch_eo_pair(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->stream);
+    }
     if (c->p.gamma5) {
         const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
         return launch_bicg_matvec_g5(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->stream,
@@ -853,14 +974,14 @@ lqcd_status enqueue_chunk(lqcd_ctx* c, int nslots, int kinds) {
             }
             CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
             CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N,
-                              c->stream, c->ru_variant, c->links_df));
+                              c->stream, c->ru_variant, c->links_df, c->eo ? 1 : 0));
             CK(launch_bicg_scalars(c->d_state, c->d_ptrs, nslots, c->stream));
             CK(launch_bicg_direction(c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
         }
         if (kinds & CH_STAB) {
             CK(launch_stab_step(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N, c->stream));
             CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->N,
-                              c->stream, c->ru_variant, c->links_df));
+                              c->stream, c->ru_variant, c->links_df, c->eo ? 1 : 0));
             CK(launch_stab_scalars(c->d_state, nslots, c->stream));
         }
     }
@@ -936,7 +1057,7 @@ lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol, bool rec_s
         if (s != LQCD_OK) return s;
     }
     CK(launch_bicg_finish(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream,
-                          c->ru_variant));
+                          c->ru_variant, c->eo ? 1 : 0));
     CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SlotState) * k, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LQCD_OK;
@@ -1026,9 +1147,8 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx* c, int k, const double* b, double* x
             }
             kb = got;
         }
-        lqcd_status s = upload(c, b + (size_t)j0 * 2 * c->N, kb, c->b_all, 0, on_device);
-        if (s != LQCD_OK) return s;
-        s = upload(c, x + (size_t)j0 * 2 * c->N, kb, c->x_hi_all, 0, on_device);
+        lqcd_status s = load_sources(c, 0, kb, b + (size_t)j0 * 2 * c->Nfull, x + (size_t)j0 * 2 * c->Nfull,
+                                     on_device);
         if (s != LQCD_OK) return s;
         int outer = 0;
         if (md != LQCD_MODE_PLAIN && c->n_def > 0) {
@@ -1090,12 +1210,14 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx* c, int k, const double* b, double* x
                 }
             }
         }
-        s = download(c, c->x_hi_all, 0, kb, x + (size_t)j0 * 2 * c->N, on_device);
+        std::vector<double> full_resid(kb, -1.0);
+        s = store_solutions(c, 0, kb, x + (size_t)j0 * 2 * c->Nfull, on_device, c->eo ? full_resid.data() : nullptr);
         if (s != LQCD_OK) return s;
         CK(cudaStreamSynchronize(c->stream));
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int j = 0; j < kb; ++j) {
-            const SlotState& st = fin[j];
+            SlotState& st = fin[j];
+            if (full_resid[j] >= 0.0) st.true_rnorm = full_resid[j] * st.bnorm;   // the full system's certificate
             lqcd_status sj = status_of(st);
             if (sj == LQCD_OK && st.bnorm > 0 && st.true_rnorm > c->p.tol * st.bnorm) sj = LQCD_ERR_NOCONV;
             if (sj != LQCD_OK && worst == LQCD_OK) worst = sj;
@@ -1406,6 +1528,7 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
         (kernel >= 10 + matvec_variants() && kernel != TIME_TILED && !(kernel >= 40 && kernel < 40 + true_resid_variants())))
         return LQCD_ERR_ARG;
     if (kernel == TIME_TILED && !c->tile_ok[k]) return LQCD_ERR_ARG;
+    if (c->eo && kernel >= 10) return LQCD_ERR_ARG;   // one operator shape
     if (kernel >= 10 && kernel < 10 + matvec_variants() &&
         !(c->p.gamma5 ? matvec_g5_variant_ok(c->g, kernel - 10) : matvec_variant_ok(c->g, kernel - 10)))
         return LQCD_ERR_ARG;
@@ -1446,7 +1569,7 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
         else if (kernel == 1) CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
         else if (kernel == 2) CK(launch_bicg_direction(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
         else CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream,
-                               c->ru_variant, c->links_df));
+                               c->ru_variant, c->links_df, c->eo ? 1 : 0));
         CK(cudaEventRecord(e1, c->stream));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -1490,6 +1613,7 @@ extern "C" lqcd_status lqcd_set_tensor_cores(lqcd_ctx* c, int on) {
 // Autotuner: time every operator-kernel variant on this lattice with a full
 // batch and keep the fastest (FP32 operator only; FP64 has one shape).
 static lqcd_status autotune(lqcd_ctx* c) {
+    if (c->eo) return LQCD_OK;   // the even-odd operator and its FP64 residual have one shape each
     {   // FP64 true-residual shape
         double best_ru = 1e300;
         for (int v = 0; v < true_resid_variants(); ++v) {
@@ -1585,6 +1709,7 @@ extern "C" lqcd_status lqcd_batch_timings(const lqcd_ctx* c, double* ms) {
 extern "C" lqcd_status lqcd_apply_pair(lqcd_ctx* c, int variant, int k, const double* p, const double* phat,
                                        double* Ap, double* Ahp, double* sigma) {
     if (!c || !p || !phat || !Ap || !Ahp || k < 1 || k > c->kmax) return LQCD_ERR_ARG;
+    if (c->eo && variant != 0) return LQCD_ERR_ARG;
     if (variant == TILED) {
         if (!c->tile_ok[k]) return LQCD_ERR_ARG;
     } else if (variant < 0 || variant >= matvec_variants() || (!c->kprec && variant != 0) ||
@@ -1670,9 +1795,7 @@ lqcd_status begin_slot(lqcd_ctx* c, int s, lqcd_mode md, double tol, bool window
 // exactly as lqcd_solve does.
 lqcd_status admit(lqcd_ctx* c, int s, const lqcd_ctx::Request& req, lqcd_mode md) {
     lqcd_ctx::SlotJob& job = c->jobs[s];
-    lqcd_status r = upload(c, req.b, 1, c->b_all + (size_t)s * c->N, 0, req.on_device);
-    if (r != LQCD_OK) return r;
-    r = upload(c, req.x, 1, c->x_hi_all + (size_t)s * c->N, 0, req.on_device);
+    lqcd_status r = load_sources(c, s, 1, req.b, req.x, req.on_device);
     if (r != LQCD_OK) return r;
     const bool two_legs = md == LQCD_MODE_DEFLATED && c->p.deftol > c->p.tol && c->n_def > 0;
     const bool windowed = md == LQCD_MODE_EIGBICG;
@@ -1698,7 +1821,7 @@ lqcd_status admit(lqcd_ctx* c, int s, const lqcd_ctx::Request& req, lqcd_mode md
 lqcd_status retire(lqcd_ctx* c, int s) {
     lqcd_ctx::SlotJob& job = c->jobs[s];
     CK(launch_bicg_finish(c->g, c->links64, c->p.kappa, c->kprec, c->d_state + s, c->d_ptrs + s, 1, c->N, c->stream,
-                          c->ru_variant));
+                          c->ru_variant, c->eo ? 1 : 0));
     CK(cudaMemcpyAsync(c->h_state + s, c->d_state + s, sizeof(SlotState), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (job.deftol_pending) {
@@ -1733,10 +1856,12 @@ lqcd_status retire(lqcd_ctx* c, int s) {
             return begin_slot(c, s, LQCD_MODE_DEFLATED, c->p.tol, false, false, true, c->p.maxiter - f.iter);
         }
     }
-    lqcd_status r = download(c, c->x_hi_all + (size_t)s * c->N, 0, 1, job.req.x, job.req.on_device);
+    double full_resid = -1.0;
+    lqcd_status r = store_solutions(c, s, 1, job.req.x, job.req.on_device, c->eo ? &full_resid : nullptr);
     if (r != LQCD_OK) return r;
     CK(cudaStreamSynchronize(c->stream));
-    const SlotState& st = c->h_state[s];
+    SlotState& st = c->h_state[s];
+    if (full_resid >= 0.0) st.true_rnorm = full_resid * st.bnorm;   // the full system's certificate
     lqcd_ctx::Finished f;
     memset(&f.info, 0, sizeof(f.info));
     f.info.iters = st.iter + job.first_iters;

@@ -71,6 +71,10 @@ struct SlotPtrs {
     double2* lam;          // restart eigenvalues (2nev)
     double2* partials;     // per-block reduction scratch of this slot
     unsigned* counters;    // last-block counters of this slot (one per kernel kind)
+    void* eo_t;            // even-odd operator: even half fields of the two hop stages
+    void* eo_th;           //   (D_eo p and (D^+)_eo phat, Krylov precision)
+    double2* eo64;         //   and of the FP64 Schur residual (D_eo x_hi)
+    const double* bnorm_ref;   // if set: ||b|| of the full system (the Schur system's tolerance reference)
 };
 
 enum CounterId { CNT_MATVEC = 0, CNT_UPDATE = 1, CNT_RU = 2, CNT_REPLACE = 3, CNT_START = 4,

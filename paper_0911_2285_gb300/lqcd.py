@@ -46,6 +46,7 @@ class Params(C.Structure):
         ("delta", C.c_double),
         ("gamma5", C.c_int),
         ("bicgstab", C.c_int),
+        ("evenodd", C.c_int),
     ]
 
 
@@ -189,7 +190,7 @@ class Solver:
 
     def __init__(self, links, dims, kappa, nev=10, m=40, n1=4, tol=1e-10, maxiter=5000,
                  precision="mixed", deftol=0.0, k_max=0, hbm_budget_bytes=0, n_def_max=0,
-                 delta=0.0, stream=None, gamma5=False, bicgstab=False):
+                 delta=0.0, stream=None, gamma5=False, bicgstab=False, evenodd=False):
         links = np.ascontiguousarray(links, dtype=np.complex128)
         self.dims = tuple(int(d) for d in dims)
         self.kappa = float(kappa)
@@ -211,6 +212,11 @@ class Solver:
         p.delta = delta
         p.gamma5 = 1 if gamma5 else 0
         p.bicgstab = 1 if bicgstab else 0
+        p.evenodd = 1 if evenodd else 0
+        self.evenodd = bool(evenodd)
+        # field length of the solver's own space (eigenvectors, lqcd_apply): the odd
+        # half lattice in an even-odd context; sources and solutions stay full (self.n)
+        self.n_space = self.n // 2 if self.evenodd else self.n
         self.params = p
         self.gamma5 = bool(gamma5)
         self.precision = precision
@@ -321,7 +327,9 @@ class Solver:
         return x
 
     def apply(self, v, dagger=False, precision="fp64"):
-        v = _as_batch(v, self.n)
+        """``A v`` (``A^+ v``) on the solver's space: the full lattice, or A_hat on the
+        odd half lattice of an even-odd context."""
+        v = _as_batch(v, self.n_space)
         out = _zeros_like(v)
         pv, dv = _ptr(v)
         po, do = _ptr(out)
@@ -335,8 +343,8 @@ class Solver:
         cnt = C.c_int(n)
         ev = np.zeros(max(n, 1), dtype=np.complex128)
         res = np.zeros(max(n, 1), dtype=np.float64)
-        ur = np.zeros((n, self.n), dtype=np.complex128) if vectors else None
-        ul = np.zeros((n, self.n), dtype=np.complex128) if vectors else None
+        ur = np.zeros((n, self.n_space), dtype=np.complex128) if vectors else None
+        ul = np.zeros((n, self.n_space), dtype=np.complex128) if vectors else None
         st = lib().lqcd_eigs(self._h, C.byref(cnt), C.c_void_p(ev.ctypes.data),
                              C.c_void_p(ur.ctypes.data) if vectors else None,
                              C.c_void_p(ul.ctypes.data) if vectors else None, C.c_void_p(res.ctypes.data))
@@ -356,8 +364,8 @@ class Solver:
 
     def apply_pair(self, p, phat, variant):
         """One launch of the operator-pair kernel shape ``variant``: ``(A p, A^+ phat, sigma)``."""
-        p = np.ascontiguousarray(p, dtype=np.complex128).reshape(-1, self.n)
-        phat = np.ascontiguousarray(phat, dtype=np.complex128).reshape(-1, self.n)
+        p = np.ascontiguousarray(p, dtype=np.complex128).reshape(-1, self.n_space)
+        phat = np.ascontiguousarray(phat, dtype=np.complex128).reshape(-1, self.n_space)
         k = p.shape[0]
         ap = np.zeros_like(p)
         ahp = np.zeros_like(phat)
@@ -380,8 +388,8 @@ class Solver:
 
     def eigspace_get(self):
         n = self.eigspace_size()
-        ur = np.zeros((n, self.n), dtype=np.complex128)
-        ul = np.zeros((n, self.n), dtype=np.complex128)
+        ur = np.zeros((n, self.n_space), dtype=np.complex128)
+        ul = np.zeros((n, self.n_space), dtype=np.complex128)
         h = np.zeros((n, n), dtype=np.complex128)
         if n:
             _check(lib().lqcd_eigspace_get(self._h, C.c_void_p(ur.ctypes.data), C.c_void_p(ul.ctypes.data),
@@ -389,8 +397,8 @@ class Solver:
         return ur, ul, h
 
     def eigspace_set(self, ur, ul):
-        ur = np.ascontiguousarray(ur, dtype=np.complex128).reshape(-1, self.n)
-        ul = np.ascontiguousarray(ul, dtype=np.complex128).reshape(-1, self.n)
+        ur = np.ascontiguousarray(ur, dtype=np.complex128).reshape(-1, self.n_space)
+        ul = np.ascontiguousarray(ul, dtype=np.complex128).reshape(-1, self.n_space)
         if ur.shape != ul.shape:
             raise ValueError("Ur and Ul must have the same shape")
         _check(lib().lqcd_eigspace_set(self._h, ur.shape[0], C.c_void_p(ur.ctypes.data),

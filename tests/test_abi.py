@@ -45,7 +45,9 @@ def test_status_strings(libpath):
 
 
 @pytest.mark.parametrize("bad", [dict(m=16, nev=8), dict(dims=(1, 4, 4, 4)), dict(tol=0.0), dict(k_max=9),
-                                 dict(kappa=-1.0), dict(m=80), dict(n_def_max=200)])
+                                 dict(kappa=-1.0), dict(m=80), dict(n_def_max=200),
+                                 dict(dims=(4, 4, 3, 4), evenodd=True), dict(evenodd=True, gamma5=True),
+                                 dict(gamma5=True, bicgstab=True)])
 def test_init_rejects_bad_parameters_without_touching_the_device(libpath, bad):
     import numpy as np
     from paper_0911_2285_gb300 import lqcd as L
