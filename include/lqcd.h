@@ -120,6 +120,11 @@ typedef struct {
                                  lqcd_apply (which applies A_hat) use half fields of 12 V / 2
                                  complex, odd sites in site order.  All extents must be even;
                                  not combinable with gamma5 or bicgstab. */
+    int no_autotune;          /* 1 = skip the init-time autotuners (no counterpart in the paper):
+                                 operator-kernel shape 0 (lqcd_set_dslash_variant pins another),
+                                 the first FP64 residual shape, and batches of k_max (8 when
+                                 k_max = 0).  Faster context creation, and kernel launches
+                                 that a profiler can count on.  0 = autotune. */
 } lqcd_params;
 
 typedef struct {
@@ -282,7 +287,7 @@ long long lqcd_kernel_launches(void);
  * slot buffers hold, repeated reps times. kernel: 0 = operator pair
  * A p, A^+ phat (Krylov precision) with the fused sigma reduction; 1 = residual
  * update; 2 = direction update; 3 = FP64 true residual + reliable-update
- * replacement; 10 + v = operator pair in kernel shape v (v < 25), 99 = the plane-
+ * replacement; 10 + v = operator pair in kernel shape v (v < 30), 99 = the plane-
  * streaming operator pair (see lqcd_dslash_variant). Leaves the slots idle. */
 lqcd_status lqcd_time_kernel(lqcd_ctx *ctx, int kernel, int k, int reps, double *avg_ms);
 
@@ -296,12 +301,21 @@ lqcd_status lqcd_time_kernel(lqcd_ctx *ctx, int kernel, int k, int reps, double 
 lqcd_status lqcd_set_tensor_cores(lqcd_ctx *ctx, int on);
 
 /* Measurement hook: the operator-kernel shape the autotuner picked at init
- * (timing every shape on this lattice with a full batch): 0..24, or 100 for
- * the plane-streaming kernel; -1 for NULL. */
+ * (timing every shape on this lattice with a full batch): 0..29, or 100 for
+ * the plane-streaming kernel; -1 for NULL. Shapes 25..29 are the 4-D brick
+ * kernels that compute every slot of a batch in one block. */
 int lqcd_dslash_variant(const lqcd_ctx *ctx);
 
+/* Pins the operator-kernel shape (0..29 or 100, as above) instead of the
+ * autotuner's choice; the iteration graphs are rebuilt on next use. Waits for
+ * the context's stream. LQCD_ERR_ARG for a shape this context cannot use
+ * (lattice extents, FP64 Krylov vectors: shape 0 only, gamma5 variant: the
+ * one-operator shapes, even-odd operator: none), LQCD_ERR_STATE while serving
+ * requests are in flight. */
+lqcd_status lqcd_set_dslash_variant(lqcd_ctx *ctx, int variant);
+
 /* Test hook: one launch of the BiCG operator-pair kernel of shape 'variant'
- * (0..24 or 100, see lqcd_dslash_variant) on k host fields p, phat (Krylov
+ * (0..29 or 100, see lqcd_dslash_variant) on k host fields p, phat (Krylov
  * precision of the context): Ap = A p, Ahp = A^+ phat (host outputs), and
  * sigma = (phat, A p) per field (k complex, may be NULL).  Uses batch slots
  * 0..k-1 and leaves them idle.  LQCD_ERR_ARG for a shape this lattice cannot

@@ -29,6 +29,9 @@ def main(argv=None):
     d.add_argument("--k", type=int, default=8)
     d.add_argument("--variants", type=int, nargs="+", default=[2, 4])
     d.add_argument("--reps", type=int, default=5)
+    d.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="skip the init autotuner: the only operator launches are the listed shapes' "
+                        "(reps timed + 1 each, in order)")
     r = sub.add_parser("restart")
     r.add_argument("--workload", default="16^3x32")
     r.add_argument("--k", type=int, default=2)
@@ -46,12 +49,13 @@ def main(argv=None):
         from seeded_inputs import WORKLOADS, workload_links
         w = WORKLOADS[args.workload]
         with Solver(workload_links(args.workload), w["dims"], w["kappa"], nev=2, m=8, n1=1, tol=1e-10,
-                    maxiter=100, precision="mixed", k_max=args.k) as s:
+                    maxiter=100, precision="mixed", k_max=args.k, autotune=args.autotune) as s:
             V = 1
             for L in w["dims"]:
                 V *= L
             alg = V * (4 * 48 + args.k * 4 * 96)
-            print(f"{args.workload}: autotuned shape {s.dslash_variant()}, algorithmic bytes {alg}")
+            tag = "autotuned" if args.autotune else "default"
+            print(f"{args.workload}: {tag} shape {s.dslash_variant()}, algorithmic bytes {alg}")
             for v in args.variants:
                 ms = s.time_kernel(10 + v, args.k, args.reps)
                 print(f"  shape {v}: {ms:.4f} ms  {alg / ms / 1e6:.0f} GB/s")

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblqcd.so")
-SOURCES = ["kernels.cu", "dslash_tiled.cu", "gemm_tc.cu", "eig.cu", "evenodd.cu", "lqcd.cu"]
+SOURCES = ["kernels.cu", "dslash_tiled.cu", "dslash_brick.cu", "dslash_staged.cu", "gemm_tc.cu", "eig.cu", "evenodd.cu", "lqcd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -589,6 +589,22 @@ bool encode_rows(CUtensorMap* m, const void* base, size_t n_complex, int rows, s
 
 }  // namespace
 
+bool encode_tensor_map_f32(void* map, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                           const uint32_t* box) {
+    if (get_encode() != cudaSuccess || rank < 1 || rank > 5) return false;
+    cuuint64_t d[5], st[4];
+    cuuint32_t b[5], e[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        b[i] = box[i];
+        e[i] = 1;
+        if (i + 1 < rank) st[i] = strides[i];
+    }
+    return g_encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
+                    const_cast<void*>(base), d, st, b, e, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool dots_tc_supported(int a, const void* X, const void* Y, size_t N) {
     return a > 0 && a <= 4 * TC_M && N > 0 && (2 * N) % TC_KT == 0 && ((uintptr_t)X & 15) == 0 &&
            ((uintptr_t)Y & 15) == 0 && get_encode() == cudaSuccess;

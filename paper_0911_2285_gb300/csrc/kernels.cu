@@ -1471,8 +1471,10 @@ static void matvec_group_launch(const Geom& g, const void* links, double kappa, 
     matvec_group_kernel<JPB, MINB><<<grid, 32 * JPB, 0, s>>>(g, links, (float)kappa, states, ptrs, nslots);
 }
 
-int matvec_variants() { return 25; }
+int matvec_variants() { return 30; }
 bool matvec_variant_ok(const Geom& g, int v) {
+    if (v == STAGED_VARIANT) return staged_variant_ok(g);
+    if (v >= 25 && v < 30) return brick_variant_ok(g, v);
     if (v == 13 || v == 14) return brick_ok(g, 4);
     if (v == 15 || v == 23) return brick_ok(g, 2);
     if (v >= 19 && v < 25) return brick_ok(g, 4);
@@ -1481,6 +1483,9 @@ bool matvec_variant_ok(const Geom& g, int v) {
 
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
                                const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant) {
+    if (prec != 0 && variant == STAGED_VARIANT) return cudaErrorInvalidValue;   // needs the context's tensor maps
+    if (prec != 0 && variant >= 25 && variant < 30)   // 4-D bricks, every slot per block (dslash_brick.cu)
+        return launch_matvec_brick(g, links, kappa, states, ptrs, nslots, s, variant);
     if (prec == 0) {
         matvec_launch<double, 128, 1, false>(g, links, kappa, states, ptrs, nslots, s);
     } else {

@@ -3,6 +3,7 @@
 // error (cudaSuccess on success).
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
 #include "solver.cuh"
 
 namespace lqcd {
@@ -103,6 +104,25 @@ cudaError_t launch_matvec_tiled(const Geom& g, const TileGeom& tg, const void* l
 int matvec_variants();
 // false when shape v cannot run on this lattice (brick shapes need Lx, Ly % 8 == 0, Lz % BZ == 0)
 bool matvec_variant_ok(const Geom& g, int v);
+// Tiled tensor map (FP32 elements, no swizzle, rank <= 5) into the 128-byte
+// CUtensorMap at map; dims innermost first, strides in bytes (rank - 1 of them).
+bool encode_tensor_map_f32(void* map, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                           const uint32_t* box);
+// Operator pair with links and spinor tiles staged in shared memory by TMA
+// (dslash_staged.cu; FP32; shape 26). The Krylov fields of all k_max slots lie
+// in one allocation krylov_base (slot s at 6 s fields); prepare_staged encodes
+// the tensor maps into maps_out (staged_maps_bytes(), 64-byte aligned).
+bool staged_variant_ok(const Geom& g);
+size_t staged_maps_bytes();
+cudaError_t prepare_staged(const Geom& g, const void* krylov_base, int kmax, const void* links32, void* maps_out);
+cudaError_t launch_matvec_staged(const Geom& g, const void* maps, double kappa, SlotState* states,
+                                 const SlotPtrs* ptrs, int nslots, int* err, int nsm, cudaStream_t s);
+constexpr int STAGED_VARIANT = 26;
+// Operator pair on 4-D bricks of 256 sites with every slot of the batch in one
+// block (dslash_brick.cu; FP32; variants 25, 27, 28, 29 of launch_bicg_matvec).
+bool brick_variant_ok(const Geom& g, int v);
+cudaError_t launch_matvec_brick(const Geom& g, const void* links, double kappa, SlotState* states,
+                                const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant);
 cudaError_t launch_bicg_matvec(const Geom& g, const void* links, double kappa, int prec,
                                SlotState* st_, const SlotPtrs* ptrs, int nslots, cudaStream_t s, int variant);
 // gamma5 variant (Sec. 4): A p only, phat = gamma5 p; shapes v with matvec_g5_variant_ok.

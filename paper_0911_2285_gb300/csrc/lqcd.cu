@@ -131,6 +131,9 @@ struct lqcd_ctx {
     int ru_variant = 0;             // FP64 true-residual kernel shape (timed at init)
     TileGeom tgeo[MAX_SLOTS + 1] = {};
     bool tile_ok[MAX_SLOTS + 1] = {};
+    bool staged_ok = false;         // shape 26: tensor maps of the Krylov fields and links encoded
+    int nsm = 0;                    // SMs of the device (grid of the staged operator kernel)
+    alignas(64) unsigned char staged_maps[2048] = {};
     int* d_err = nullptr;           // device error word of the bounded waits
     std::vector<double> tune_ms;    // autotuner timings per variant
 
@@ -524,10 +527,21 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     if ((e = prepare_tiled_kernel()) != cudaSuccess) { set_error("prepare_tiled_kernel", e); return fail(LQCD_ERR_CUDA); }
     for (int n = 1; n <= c->kmax; ++n)
         c->tile_ok[n] = c->kprec && !c->p.gamma5 && !c->eo && tiled_plan(c->g, n, &c->tgeo[n]);
-    st = autotune(c);
+    if (c->kprec && !c->p.gamma5 && !c->eo && staged_variant_ok(c->g) && staged_maps_bytes() <= sizeof(c->staged_maps)) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) == cudaSuccess)
+            e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = prepare_staged(c->g, c->vec_all, c->kmax, c->links32, c->staged_maps);
+        // a lattice or device the tensor maps cannot describe keeps the other shapes
+        c->staged_ok = e == cudaSuccess;
+        if (e == cudaErrorInvalidValue) { cudaGetLastError(); e = cudaSuccess; }
+        if (e != cudaSuccess) { set_error("prepare_staged", e); return fail(LQCD_ERR_CUDA); }
+    }
+    st = c->p.no_autotune ? LQCD_OK : autotune(c);
     if (st != LQCD_OK) return fail(st);
     c->kbatch = c->kmax;
-    if (c->k_auto) {
+    if (c->k_auto && !c->p.no_autotune) {
         st = autotune_batch(c);
         if (st != LQCD_OK) return fail(st);
     }
@@ -935,6 +949,14 @@ extern "C" lqcd_status lqcd_deflate(lqcd_ctx* c, int k, const double* b, double*
 // ============================================================ the solve
 namespace {
 
+// Operator-kernel shape v usable on this context (FP32 Krylov vectors; the
+// gamma5 variant has its own list; the staged shape needs its tensor maps).
+bool shape_ok(const lqcd_ctx* c, int v) {
+    if (c->p.gamma5) return matvec_g5_variant_ok(c->g, v);
+    if (v == STAGED_VARIANT && !c->staged_ok) return false;
+    return matvec_variant_ok(c->g, v);
+}
+
 // The operator pair of one iteration in the autotuned kernel shape.
 cudaError_t launch_matvec(lqcd_ctx* c, int nslots, int variant) {
     if (c->eo) {
@@ -949,6 +971,9 @@ cudaError_t launch_matvec(lqcd_ctx* c, int nslots, int variant) {
     if (variant == TILED && c->tile_ok[nslots])
         return launch_matvec_tiled(c->g, c->tgeo[nslots], c->links32, c->p.kappa, c->d_state, c->d_ptrs, c->d_err,
                                    c->stream);
+    if (variant == STAGED_VARIANT && c->kprec && c->staged_ok)
+        return launch_matvec_staged(c->g, c->staged_maps, c->p.kappa, c->d_state, c->d_ptrs, nslots, c->d_err, c->nsm,
+                                    c->stream);
     const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
     return launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, nslots, c->stream,
                               variant == TILED ? 0 : variant);
@@ -1529,9 +1554,7 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
         return LQCD_ERR_ARG;
     if (kernel == TIME_TILED && !c->tile_ok[k]) return LQCD_ERR_ARG;
     if (c->eo && kernel >= 10) return LQCD_ERR_ARG;   // one operator shape
-    if (kernel >= 10 && kernel < 10 + matvec_variants() &&
-        !(c->p.gamma5 ? matvec_g5_variant_ok(c->g, kernel - 10) : matvec_variant_ok(c->g, kernel - 10)))
-        return LQCD_ERR_ARG;
+    if (kernel >= 10 && kernel < 10 + matvec_variants() && !shape_ok(c, kernel - 10)) return LQCD_ERR_ARG;
     const int ru_saved = c->ru_variant;
     if (kernel >= 40 && kernel < 40 + true_resid_variants()) {   // reliable update with FP64 shape v
         c->ru_variant = kernel - 40;
@@ -1556,16 +1579,13 @@ static lqcd_status time_kernel_impl(lqcd_ctx* c, int kernel, int k, int reps, do
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const void* links = c->kprec ? (const void*)c->links32 : (const void*)c->links64;
     double total = 0.0;
     for (int r = 0; r < reps; ++r) {
         CK(cudaMemcpyAsync(c->d_state, tmpl.data(), sizeof(SlotState) * c->kmax, cudaMemcpyHostToDevice, c->stream));
         CK(cudaEventRecord(e0, c->stream));
         if (kernel == 0) CK(launch_matvec(c, k, c->dslash_variant));
         else if (kernel == TIME_TILED) CK(launch_matvec(c, k, TILED));
-        else if (kernel >= 10 && c->p.gamma5) CK(launch_matvec(c, k, kernel - 10));
-        else if (kernel >= 10) CK(launch_bicg_matvec(c->g, links, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k,
-                                                     c->stream, kernel - 10));
+        else if (kernel >= 10) CK(launch_matvec(c, k, kernel - 10));
         else if (kernel == 1) CK(launch_bicg_update(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
         else if (kernel == 2) CK(launch_bicg_direction(c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream));
         else CK(launch_bicg_ru(c->g, c->links64, c->p.kappa, c->kprec, c->d_state, c->d_ptrs, k, c->N, c->stream,
@@ -1593,6 +1613,15 @@ extern "C" lqcd_status lqcd_time_kernel(lqcd_ctx* c, int kernel, int k, int reps
 
 extern "C" int lqcd_dslash_variant(const lqcd_ctx* c) { return c ? c->dslash_variant : -1; }
 
+static void drop_graphs(lqcd_ctx* c) {
+    for (int i = 0; i <= MAX_SLOTS; ++i)   // the iteration graphs hold the old kernels
+        for (int j = 0; j < 8; ++j)
+            if (c->graphs[i][j]) {
+                cudaGraphExecDestroy(c->graphs[i][j]);
+                c->graphs[i][j] = nullptr;
+            }
+}
+
 extern "C" lqcd_status lqcd_set_tensor_cores(lqcd_ctx* c, int on) {
     if (!c) return LQCD_ERR_ARG;
     if (c->session_busy()) {
@@ -1601,12 +1630,26 @@ extern "C" lqcd_status lqcd_set_tensor_cores(lqcd_ctx* c, int on) {
     }
     CK(cudaStreamSynchronize(c->stream));
     c->use_tc = on ? 1 : 0;
-    for (int i = 0; i <= MAX_SLOTS; ++i)   // the iteration graphs hold the old kernels
-        for (int j = 0; j < 8; ++j)
-            if (c->graphs[i][j]) {
-                cudaGraphExecDestroy(c->graphs[i][j]);
-                c->graphs[i][j] = nullptr;
-            }
+    drop_graphs(c);
+    return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_set_dslash_variant(lqcd_ctx* c, int variant) {
+    if (!c) return LQCD_ERR_ARG;
+    if (c->session_busy()) {
+        g_last_error = "lqcd_set_dslash_variant: requests are in flight";
+        return LQCD_ERR_STATE;
+    }
+    const bool ok = variant == TILED ? (c->kprec && !c->eo && !c->p.gamma5 && c->tile_ok[c->kmax])
+                                     : variant >= 0 && variant < matvec_variants() && !c->eo &&
+                                           (c->kprec || variant == 0) && shape_ok(c, variant);
+    if (!ok) {
+        g_last_error = "lqcd_set_dslash_variant: shape not available on this context";
+        return LQCD_ERR_ARG;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->dslash_variant = variant;
+    drop_graphs(c);
     return LQCD_OK;
 }
 
@@ -1632,7 +1675,7 @@ static lqcd_status autotune(lqcd_ctx* c) {
     double best = 1e300;
     for (int v = 0; v < nv; ++v) {
         double ms = 0.0;
-        if (!(c->p.gamma5 ? matvec_g5_variant_ok(c->g, v) : matvec_variant_ok(c->g, v))) {
+        if (!shape_ok(c, v)) {
             c->tune_ms[v] = -1.0;
             continue;
         }
@@ -1713,7 +1756,7 @@ extern "C" lqcd_status lqcd_apply_pair(lqcd_ctx* c, int variant, int k, const do
     if (variant == TILED) {
         if (!c->tile_ok[k]) return LQCD_ERR_ARG;
     } else if (variant < 0 || variant >= matvec_variants() || (!c->kprec && variant != 0) ||
-               !(c->p.gamma5 ? matvec_g5_variant_ok(c->g, variant) : matvec_variant_ok(c->g, variant))) {
+               !shape_ok(c, variant)) {
         return LQCD_ERR_ARG;
     }
     const size_t fb = 2 * c->N;   // doubles per host field

@@ -47,6 +47,7 @@ class Params(C.Structure):
         ("gamma5", C.c_int),
         ("bicgstab", C.c_int),
         ("evenodd", C.c_int),
+        ("no_autotune", C.c_int),
     ]
 
 
@@ -128,6 +129,8 @@ def lib():
         L.lqcd_wait_flag.restype = C.c_int
         L.lqcd_dslash_variant.argtypes = [vp]
         L.lqcd_dslash_variant.restype = C.c_int
+        L.lqcd_set_dslash_variant.argtypes = [vp, C.c_int]
+        L.lqcd_set_dslash_variant.restype = C.c_int
         for name in ("lqcd_eigbicg_init", "lqcd_solve", "lqcd_deflate", "lqcd_eigs", "lqcd_apply",
                      "lqcd_eigspace_get", "lqcd_eigspace_set", "lqcd_last_window", "lqcd_small_eig",
                      "lqcd_restart_coefficients"):
@@ -190,7 +193,7 @@ class Solver:
 
     def __init__(self, links, dims, kappa, nev=10, m=40, n1=4, tol=1e-10, maxiter=5000,
                  precision="mixed", deftol=0.0, k_max=0, hbm_budget_bytes=0, n_def_max=0,
-                 delta=0.0, stream=None, gamma5=False, bicgstab=False, evenodd=False):
+                 delta=0.0, stream=None, gamma5=False, bicgstab=False, evenodd=False, autotune=True):
         links = np.ascontiguousarray(links, dtype=np.complex128)
         self.dims = tuple(int(d) for d in dims)
         self.kappa = float(kappa)
@@ -213,6 +216,7 @@ class Solver:
         p.gamma5 = 1 if gamma5 else 0
         p.bicgstab = 1 if bicgstab else 0
         p.evenodd = 1 if evenodd else 0
+        p.no_autotune = 0 if autotune else 1
         self.evenodd = bool(evenodd)
         # field length of the solver's own space (eigenvectors, lqcd_apply): the odd
         # half lattice in an even-odd context; sources and solutions stay full (self.n)
@@ -380,8 +384,12 @@ class Solver:
         _check(lib().lqcd_set_tensor_cores(self._h, 1 if on else 0), "lqcd_set_tensor_cores")
 
     def dslash_variant(self):
-        """Operator-kernel shape chosen by the autotuner."""
+        """Operator-kernel shape chosen by the autotuner (or pinned)."""
         return lib().lqcd_dslash_variant(self._h)
+
+    def set_dslash_variant(self, variant):
+        """Pin the operator-kernel shape (LQCDError if this context cannot use it)."""
+        _check(lib().lqcd_set_dslash_variant(self._h, int(variant)), "lqcd_set_dslash_variant")
 
     def eigspace_size(self):
         return lib().lqcd_eigspace_size(self._h)

@@ -4,7 +4,7 @@ thread blocks, L = 2 wrap-around, odd/asymmetric extents and the largest workloa
 import numpy as np
 import pytest
 
-from tests.gpu_util import random_field, rel, small_problem, workload
+from tests.gpu_util import random_field, rel, small_problem, true_resid, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -75,7 +75,7 @@ def test_operator_pair_kernels_match_oracle(name):
             p = np.stack([random_field(op.n, 20 + i) for i in range(k)])
             ph = np.stack([random_field(op.n, 40 + i) for i in range(k)])
             refs = [(op.apply(p[i]), op.apply_dag(ph[i])) for i in range(k)]
-            for variant in list(range(25)) + [100]:
+            for variant in list(range(30)) + [100]:
                 ap, ahp, sig = s.apply_pair(p, ph, variant)
                 for i in range(k):
                     assert rel(ap[i], refs[i][0]) <= 2e-6, (variant, i)
@@ -85,13 +85,53 @@ def test_operator_pair_kernels_match_oracle(name):
 
 
 def test_brick_shapes_rejected_on_small_extents():
-    """Brick site orders need Lx, Ly divisible by 8: refused on 4^4, not run."""
+    """Brick site orders need extents divisible by the brick's: refused on 4^4,
+    not run (8 x 8 bricks, the 8 x 4 x 4 x 2 and 4 x 4 x 8 x 2 4-D bricks, the
+    TMA-staged 8 x 4 x 4 x 2 bricks). The
+    4^4 4-D brick covers the whole lattice, so every neighbour wraps into the
+    block's own brick and every backward link comes from its face buffer."""
     from paper_0911_2285_gb300 import Solver, lqcd
     w, links, op = workload("4^4")
-    with Solver(links, w["dims"], w["kappa"], nev=1, m=3, precision="mixed", k_max=1, n_def_max=1) as s:
+    with Solver(links, w["dims"], w["kappa"], nev=1, m=3, precision="mixed", k_max=2, n_def_max=1) as s:
         p = random_field(op.n, 1)
-        for variant in (13, 14, 15, 19, 20, 21, 22, 23, 24):
+        for variant in (13, 14, 15, 19, 20, 21, 22, 23, 24, 26, 27, 28):
             with pytest.raises(lqcd.LQCDError):
                 s.apply_pair(p, p, variant)
-        ap, _, _ = s.apply_pair(p, p, 2)
-        assert rel(ap[0], op.apply(p)) <= 2e-6
+            with pytest.raises(lqcd.LQCDError):
+                s.set_dslash_variant(variant)
+        ph = random_field(op.n, 2)
+        for variant in (2, 25, 29):
+            ap, ahp, sig = s.apply_pair(np.stack([p, ph]), np.stack([ph, p]), variant)
+            assert rel(ap[0], op.apply(p)) <= 2e-6 and rel(ap[1], op.apply(ph)) <= 2e-6
+            assert rel(ahp[0], op.apply_dag(ph)) <= 2e-6 and rel(ahp[1], op.apply_dag(p)) <= 2e-6
+            sref = np.vdot(ph, op.apply(p))
+            assert abs(sig[0] - sref) <= 1e-5 * abs(sref)
+
+
+@pytest.mark.parametrize("variant", [25, 26, 27])
+def test_brick_shape_full_batch_solve(variant):
+    """The 4-D brick shapes (every slot of the batch in one block; 26 stages
+    links and spinor tiles in shared memory by TMA) in a full
+    batch of 8 mixed-precision BiCG solves, pinned instead of the autotuner's
+    pick: slots converge at different iterations, so later launches run with a
+    partial mask of slots; every solution meets the FP64 residual with the
+    oracle's operator, and the iteration counts match the per-slot shape's to
+    FP32 rounding (+-2)."""
+    from paper_0911_2285_gb300 import Solver
+    from seeded_inputs import workload_source
+    w, links, op = workload("8^4")
+    b = np.stack([workload_source("8^4", 300 + i) for i in range(8)])
+    b[3] *= 1e-3   # a scaled source: same iterations, different magnitudes in one batch
+    b[5] = random_field(op.n, 77)
+    kw = dict(nev=w["nev"], m=w["m"], n1=w["n1"], tol=1e-10, maxiter=2000, precision="mixed", k_max=8)
+    with Solver(links, w["dims"], w["kappa"], **kw) as s:
+        s.set_dslash_variant(2)
+        _, ref, _ = s.solve(b, mode="plain")
+        s.set_dslash_variant(variant)
+        assert s.dslash_variant() == variant
+        x, info, status = s.solve(b, mode="plain")
+    assert status == 0
+    for i in range(8):
+        assert true_resid(op, b[i], x[i]) <= 1e-10, i
+        assert abs(info[i]["iters"] - ref[i]["iters"]) <= 2, (i, info[i]["iters"], ref[i]["iters"])
+    assert len({i["iters"] for i in info}) > 1
