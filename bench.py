@@ -147,7 +147,8 @@ def recorded_traffic(kernel_tag, variant):
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "dslash.cuh", "common.cuh", "solver.cuh"):
+    for f in ("kernels.cu", "dslash.cuh", "common.cuh", "solver.cuh", "dslash_staged.cu", "dslash_brick.cu",
+              "async.cuh", "reduce.cuh"):
         h.update(open(os.path.join(ROOT, "paper_0911_2285_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
