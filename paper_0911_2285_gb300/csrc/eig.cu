@@ -48,29 +48,41 @@ __device__ int schur(double2* A, double2* Q, int n, int lda, double2* v /* n */,
     // Q = I
     for (int e = tid; e < n * lda; e += blockDim.x) Q[e] = ((e / lda) == (e % lda)) ? cone() : czero();
     __syncthreads();
-    // Householder reduction to upper Hessenberg.
+    // Householder reduction to upper Hessenberg. A column with nothing below its
+    // subdiagonal is skipped, and a reflection spans only the rows up to the
+    // column's last nonzero: the projected matrices of eigBiCG are tridiagonal,
+    // or after a restart diagonal + coupling arrow + tridiagonal, so most
+    // columns need no work.
     for (int k = 0; k + 2 < n; ++k) {
-        // v = x + e^{i theta} ||x|| e1, x = A[k+1:n, k]
+        // v = x + e^{i theta} ||x|| e1, x = A[k+1:last+1, k]
         if (tid == 0) {
-            double nrm2 = 0.0;
-            for (int i = k + 1; i < n; ++i) nrm2 += cabs2(A[i * lda + k]);
+            double nrm2 = 0.0, tail = 0.0;
+            int last = k + 1;
+            for (int i = k + 1; i < n; ++i) {
+                const double a2 = cabs2(A[i * lda + k]);
+                nrm2 += a2;
+                if (i >= k + 2) tail += a2;
+                if (a2 != 0.0) last = i;
+            }
             double alpha = sqrt(nrm2);
             double2 x0 = A[(k + 1) * lda + k];
             double ax0 = cabs_(x0);
             double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : cone();
-            sh[0] = alpha;
+            sh[0] = tail > 0.0 ? alpha : 0.0;   // 0: skip the step
             sh[1] = alpha > 0.0 ? 1.0 / (alpha * (alpha + ax0)) : 0.0;   // tau = 2/||v||^2
             sh[2] = ph.x; sh[3] = ph.y;
+            sh[5] = (double)last;
         }
         __syncthreads();
         double alpha = sh[0], tau = sh[1];
         double2 ph = make_double2(sh[2], sh[3]);
+        const int last = (int)sh[5];
         if (alpha == 0.0) { __syncthreads(); continue; }
-        for (int i = k + 1 + tid; i < n; i += blockDim.x) v[i - k - 1] = A[i * lda + k];
+        for (int i = k + 1 + tid; i <= last; i += blockDim.x) v[i - k - 1] = A[i * lda + k];
         __syncthreads();
         if (tid == 0) v[0] = v[0] + alpha * ph;
         __syncthreads();
-        const int len = n - k - 1;
+        const int len = last - k;
         // rows k+1..n-1 of A: A -= tau v (v^H A), columns k..n-1
         for (int j = k + tid; j < n; j += blockDim.x) {
             double2 w = czero();
@@ -88,7 +100,7 @@ __device__ int schur(double2* A, double2* Q, int n, int lda, double2* v /* n */,
             for (int l = 0; l < len; ++l) row[k + 1 + l] = row[k + 1 + l] - mulc(u, v[l]);
         }
         __syncthreads();
-        for (int i = k + 2 + tid; i < n; i += blockDim.x) A[i * lda + k] = czero();
+        for (int i = k + 2 + tid; i <= last; i += blockDim.x) A[i * lda + k] = czero();
         __syncthreads();
     }
     // Frobenius norm for the negligibility tests.

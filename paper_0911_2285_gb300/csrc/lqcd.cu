@@ -131,6 +131,7 @@ struct lqcd_ctx {
     int ru_variant = 0;             // FP64 true-residual kernel shape (timed at init)
     TileGeom tgeo[MAX_SLOTS + 1] = {};
     bool tile_ok[MAX_SLOTS + 1] = {};
+    long long deflations_discarded = 0;   // oblique projections undone (deflate_range)
     bool staged_ok = false;         // shape 26: tensor maps of the Krylov fields and links encoded
     int nsm = 0;                    // SMs of the device (grid of the staged operator kernel)
     alignas(64) unsigned char staged_maps[2048] = {};
@@ -764,15 +765,30 @@ extern "C" lqcd_status lqcd_apply(lqcd_ctx* c, int dagger, lqcd_precision prec, 
 // ============================================================ deflation
 namespace {
 
+// Residual growth beyond which an oblique projection is discarded (see deflate_range).
+constexpr double DEFLATE_GROWTH_MAX = 4.0;
+
 // x_hi[j] += U_r H^{-1} U_l^H (b_j - A x_hi[j]) for slots s0 .. s0+k-1
-// (precise: FP64 residual, see residual_fields).
-lqcd_status deflate_range(lqcd_ctx* c, int s0, int k, bool precise = false) {
+// (precise: FP64 residual, see residual_fields). first (the first deflation of
+// a source's initial guess) in the gamma5 variant: a slot whose residual norm
+// the projection multiplies by more than DEFLATE_GROWTH_MAX keeps its guess.
+// The left vectors are gamma5 images of the right ones, so U_l^H A U_r is close
+// to the indefinite Hermitian U_r^H gamma5 A U_r and can be nearly singular; the
+// correction is then noise that the FP32 gamma5 recursion may not recover from
+// (the general BiCG does). With the guard, rt holds b - A x_hi on return.
+lqcd_status deflate_range(lqcd_ctx* c, int s0, int k, bool precise = false, bool first = false) {
     const int n = c->n_def;
     if (n == 0 || k == 0) return LQCD_OK;
+    const bool guard = first && c->p.gamma5;
     double2* xh = c->x_hi_all + (size_t)s0 * c->N;
     double2* rt = c->rt_all + (size_t)s0 * c->N;
-    lqcd_status s = residual_fields(c, k, xh, rt, c->b_all + (size_t)s0 * c->N, precise);
+    const double2* bs = c->b_all + (size_t)s0 * c->N;
+    lqcd_status s = residual_fields(c, k, xh, rt, bs, precise);
     if (s != LQCD_OK) return s;
+    double2* scr = c->dsmall + (size_t)MAX_SMALL * MAX_SMALL * 6;   // norms before / after, reverting C
+    double* nrm = reinterpret_cast<double*>(scr);
+    double2* Crev = scr + MAX_SLOTS;
+    if (guard) CK(launch_norms(k, rt, 0, c->N, nrm, c->mdscratch, c->mdscratch_elems, c->stream));
     double2* C = c->dsmall;   // n x k, ld k
     const void* R = rt;
     int rp = 0;
@@ -785,9 +801,38 @@ lqcd_status deflate_range(lqcd_ctx* c, int s0, int k, bool precise = false) {
     CK(launch_multidot(n, c->Ul, c->kprec, k, R, rp, c->N, C, k, 0, c->mdscratch, c->mdscratch_elems, c->stream, c->d_err, c->use_tc));
     CK(launch_lu_solve(n, c->Hlu, c->n_def_max, c->Hpiv, 0, k, C, k, c->stream));
     CK(launch_vupdate(n, c->Ur, c->kprec, C, k, k, xh, 0, 0, c->N, c->stream));
+    if (!guard) return LQCD_OK;
+    s = residual_fields(c, k, xh, rt, bs, precise);
+    if (s != LQCD_OK) return s;
+    CK(launch_norms(k, rt, 0, c->N, nrm + MAX_SLOTS, c->mdscratch, c->mdscratch_elems, c->stream));
+    double hn[2 * MAX_SLOTS];
+    CK(cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    bool bad[MAX_SLOTS] = {}, any = false;
+    for (int j = 0; j < k; ++j) {
+        bad[j] = !(hn[MAX_SLOTS + j] <= DEFLATE_GROWTH_MAX * hn[j]);
+        any = any || bad[j];
+    }
+    if (any) {   // take the correction back from those slots: x_hi -= U_r C
+        std::vector<double2> hc((size_t)n * k);
+        CK(cudaMemcpyAsync(hc.data(), C, sizeof(double2) * n * k, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < k; ++j) {
+                double2& v = hc[(size_t)i * k + j];
+                v = bad[j] ? make_double2(-v.x, -v.y) : make_double2(0.0, 0.0);
+            }
+        CK(cudaMemcpyAsync(Crev, hc.data(), sizeof(double2) * n * k, cudaMemcpyHostToDevice, c->stream));
+        CK(launch_vupdate(n, c->Ur, c->kprec, Crev, k, k, xh, 0, 0, c->N, c->stream));
+        s = residual_fields(c, k, xh, rt, bs, precise);
+        if (s != LQCD_OK) return s;
+        for (int j = 0; j < k; ++j) c->deflations_discarded += bad[j] ? 1 : 0;
+    }
     return LQCD_OK;
 }
-lqcd_status deflate_slots(lqcd_ctx* c, int k, bool precise = false) { return deflate_range(c, 0, k, precise); }
+lqcd_status deflate_slots(lqcd_ctx* c, int k, bool precise = false, bool first = false) {
+    return deflate_range(c, 0, k, precise, first);
+}
 
 lqcd_status refactor(lqcd_ctx* c) {
     const int n = c->n_def, ld = c->n_def_max;
@@ -1177,7 +1222,7 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx* c, int k, const double* b, double* x
         if (s != LQCD_OK) return s;
         int outer = 0;
         if (md != LQCD_MODE_PLAIN && c->n_def > 0) {
-            s = deflate_slots(c, kb);
+            s = deflate_slots(c, kb, false, true);
             if (s != LQCD_OK) return s;
         }
         std::vector<SlotState> first;
@@ -1809,9 +1854,9 @@ namespace {
 // stop at the recursive convergence candidate); precise: FP64 residuals for
 // the deflation and the start (a leg that continues from an earlier iterate).
 lqcd_status begin_slot(lqcd_ctx* c, int s, lqcd_mode md, double tol, bool windowed, bool rec_stop, bool precise,
-                       int maxiter, bool stab = false) {
+                       int maxiter, bool stab = false, bool first = false) {
     if (md != LQCD_MODE_PLAIN && c->n_def > 0) {
-        lqcd_status r = deflate_range(c, s, 1, precise);
+        lqcd_status r = deflate_range(c, s, 1, precise, first);
         if (r != LQCD_OK) return r;
     }
     SlotState& st = c->h_state[s];
@@ -1844,7 +1889,7 @@ lqcd_status admit(lqcd_ctx* c, int s, const lqcd_ctx::Request& req, lqcd_mode md
     const bool windowed = md == LQCD_MODE_EIGBICG;
     const bool eig_legs = windowed && c->kprec;   // mixed eigBiCG: window leg, then correction leg
     r = begin_slot(c, s, md, two_legs ? c->p.deftol : c->p.tol, windowed, eig_legs, false, c->p.maxiter,
-                   c->p.bicgstab != 0);
+                   c->p.bicgstab != 0, true);
     if (r != LQCD_OK) return r;
     job.busy = true;
     job.req = req;

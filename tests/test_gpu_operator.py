@@ -61,6 +61,36 @@ def test_apply_full_size_24x24x24x64_sampled():
         assert rel(out32, ref) <= 2e-6
 
 
+def test_operator_pair_full_size_autotuned_batch():
+    """The launch configuration the benchmark times: 24^3x64, a batch of 8 slots,
+    the operator-pair shape the autotuner picks. Slots 0 and 7 hold independent
+    random fields, compared with the oracle's A and A^+ element by element
+    (FP32 fields: 2e-6) with sigma = (phat, A p); slots 1..6 hold complex
+    multiples of slot 0's fields, so their outputs must be the same multiples of
+    slot 0's (a slot reading or writing another slot's data fails this)."""
+    from paper_0911_2285_gb300 import Solver
+    w, links, op = workload("24^3x64")
+    p0, p7 = random_field(op.n, 21), random_field(op.n, 27)
+    h0, h7 = random_field(op.n, 41), random_field(op.n, 47)
+    c = np.exp(1j * np.arange(1, 7)) * np.arange(2, 8) / 4.0
+    p = np.stack([p0] + [ci * p0 for ci in c] + [p7])
+    ph = np.stack([h0] + [ci * h0 for ci in c] + [h7])
+    with Solver(links, w["dims"], w["kappa"], nev=4, m=12, precision="mixed", k_max=8) as s:
+        shape = s.dslash_variant()
+        ap, ahp, sig = s.apply_pair(p, ph, shape)
+    del p, ph
+    for i, (pi, hi) in ((0, (p0, h0)), (7, (p7, h7))):
+        ref, refd = op.apply(pi), op.apply_dag(hi)
+        assert rel(ap[i], ref) <= 2e-6, (shape, i)
+        assert rel(ahp[i], refd) <= 2e-6, (shape, i)
+        sref = np.vdot(hi, ref)
+        assert abs(sig[i] - sref) <= 1e-5 * abs(sref), (shape, i)
+    for j, ci in enumerate(c, start=1):
+        assert rel(ap[j], ci * ap[0]) <= 1e-6, (shape, j)
+        assert rel(ahp[j], ci * ahp[0]) <= 1e-6, (shape, j)
+        assert abs(sig[j] - abs(ci) ** 2 * sig[0]) <= 1e-5 * abs(ci) ** 2 * abs(sig[0]), (shape, j)
+
+
 @pytest.mark.parametrize("name", ["8^4", "16^3x32"])
 def test_operator_pair_kernels_match_oracle(name):
     """Every shape of the BiCG operator-pair kernel (the autotuner's candidates:
