@@ -157,11 +157,25 @@ __global__ void __launch_bounds__(EO_THREADS) eo_reconstruct_kernel(Geom g, cons
 }
 
 // ------------------------------------------------------------ BiCG kernels
+// The pair kernels: a block takes a contiguous run of THREADS-site units of
+// the half lattice (neighbouring sites stay on one SM; FP32: 256 threads, two
+// blocks per SM, two units per block, like the full operator's best
+// gather-through-L1 shape).
+struct HalfRun {
+    int u0, u1;
+    __device__ __forceinline__ HalfRun(int Vh, int threads, int nsb, int sblock) {
+        const int nunits = (Vh + threads - 1) / threads;
+        const int per = (nunits + nsb - 1) / nsb;
+        u0 = sblock * per;
+        u1 = min(nunits, u0 + per);
+    }
+};
+
 // Operator pair of one BiCG iteration on A_hat, stage 1 (one thread per (half
 // site, slot)): t = D_eo p, that = (D^+)_eo phat into the slot's stage buffers.
-template <typename S>
-__global__ void __launch_bounds__(EO_THREADS) eo_pair1_kernel(Geom g, const void* links, SlotState* states,
-                                                             const SlotPtrs* ptrs, int nslots) {
+template <typename S, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) eo_pair1_kernel(Geom g, const void* links, SlotState* states,
+                                                                const SlotPtrs* ptrs, int nslots) {
     const int slot = blockIdx.x % nslots, sblock = blockIdx.x / nslots, nsb = gridDim.x / nslots;
     const SlotState& st = states[slot];
     const SlotPtrs& P = ptrs[slot];
@@ -169,7 +183,10 @@ __global__ void __launch_bounds__(EO_THREADS) eo_pair1_kernel(Geom g, const void
     const int Vh = g.V / 2;
     typename LinkSel<S>::type U{reinterpret_cast<decltype(U.u)>(links), g.V};
     HalfIn<S> inp{P.p, Vh}, inh{P.phat, Vh};
-    for (int h = sblock * blockDim.x + threadIdx.x; h < Vh; h += nsb * blockDim.x) {
+    const HalfRun run(Vh, THREADS, nsb, sblock);
+    for (int u = run.u0; u < run.u1; ++u) {
+        const int h = u * THREADS + (int)threadIdx.x;
+        if (h >= Vh) continue;
         const int s = eo_site(g, h, 0);
         cplx<S> a[12], b[12];
         hop_site_pair<S>(g, U, inp, inh, s, a, b);
@@ -180,9 +197,9 @@ __global__ void __launch_bounds__(EO_THREADS) eo_pair1_kernel(Geom g, const void
 
 // Stage 2: A_hat p = p - k^2 D_oe t, A_hat^+ phat = phat - k^2 (D^+)_oe that, and
 // sigma = (phat, A_hat p), alpha = rho / sigma in the last block.
-template <typename S>
-__global__ void __launch_bounds__(EO_THREADS) eo_pair2_kernel(Geom g, const void* links, double kappa,
-                                                             SlotState* states, const SlotPtrs* ptrs, int nslots) {
+template <typename S, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) eo_pair2_kernel(Geom g, const void* links, double kappa,
+                                                                SlotState* states, const SlotPtrs* ptrs, int nslots) {
     const int slot = blockIdx.x % nslots, sblock = blockIdx.x / nslots, nsb = gridDim.x / nslots;
     SlotState& st = states[slot];
     const SlotPtrs& P = ptrs[slot];
@@ -193,7 +210,10 @@ __global__ void __launch_bounds__(EO_THREADS) eo_pair2_kernel(Geom g, const void
     HalfIn<S> int_{P.eo_t, Vh}, inth{P.eo_th, Vh};
     const S k2 = (S)(kappa * kappa);
     Acc<S> sacc;   // sigma, |phat|^2, |Ap|^2
-    for (int h = sblock * blockDim.x + threadIdx.x; h < Vh; h += nsb * blockDim.x) {
+    const HalfRun run(Vh, THREADS, nsb, sblock);
+    for (int u = run.u0; u < run.u1; ++u) {
+        const int h = u * THREADS + (int)threadIdx.x;
+        if (h >= Vh) continue;
         const int s = eo_site(g, h, 1);
         cplx<S> a[12], b[12], self[12];
         hop_site_pair<S>(g, U, int_, inth, s, a, b);
@@ -315,13 +335,16 @@ cudaError_t launch_eo_reconstruct(const Geom& g, const void* links64, double kap
 
 cudaError_t launch_eo_pair(const Geom& g, const void* links, double kappa, int prec, SlotState* states,
                            const SlotPtrs* ptrs, int nslots, cudaStream_t st) {
-    const int grid = eo_blocks(g.V / 2) * nslots;
     if (prec == 0) {
-        eo_pair1_kernel<double><<<grid, EO_THREADS, 0, st>>>(g, links, states, ptrs, nslots);
-        eo_pair2_kernel<double><<<grid, EO_THREADS, 0, st>>>(g, links, kappa, states, ptrs, nslots);
+        const int grid = eo_blocks(g.V / 2) * nslots;
+        eo_pair1_kernel<double, EO_THREADS, 1><<<grid, EO_THREADS, 0, st>>>(g, links, states, ptrs, nslots);
+        eo_pair2_kernel<double, EO_THREADS, 1><<<grid, EO_THREADS, 0, st>>>(g, links, kappa, states, ptrs, nslots);
     } else {
-        eo_pair1_kernel<float><<<grid, EO_THREADS, 0, st>>>(g, links, states, ptrs, nslots);
-        eo_pair2_kernel<float><<<grid, EO_THREADS, 0, st>>>(g, links, kappa, states, ptrs, nslots);
+        constexpr int T = 256, UNITS = 2;
+        int nb = (g.V / 2 + T * UNITS - 1) / (T * UNITS);
+        if (nb > PARTIAL_STRIDE / 2) nb = PARTIAL_STRIDE / 2;
+        eo_pair1_kernel<float, T, 2><<<nb * nslots, T, 0, st>>>(g, links, states, ptrs, nslots);
+        eo_pair2_kernel<float, T, 2><<<nb * nslots, T, 0, st>>>(g, links, kappa, states, ptrs, nslots);
     }
     count_launches(2);
     return cudaGetLastError();
