@@ -28,13 +28,40 @@ __device__ __forceinline__ double2 cone() { return make_double2(1.0, 0.0); }
 // |re| + |im|: the modulus surrogate used for negligibility tests (no sqrt).
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
 
+// 1/sqrt(a) for a > 0 in FP64. FP64 arithmetic issues at 1/64 of the FP32 rate
+// on this GPU, so the library's FP64 square root and divide are long serial
+// chains; inside FP32's normal range, an FP32 reciprocal square root seeds
+// Newton-Raphson for f(y) = 1/y^2 - a, y <- y (3 - a y^2) / 2, which doubles
+// the correct bits per step: two steps take the FP32 seed (about 22 bits) to
+// FP64 accuracy. Outside that range: 1 / sqrt(a).
+__device__ __forceinline__ double rsqrt_fp64(double a) {
+    if (!(a > 1e-30 && a < 1e30)) return 1.0 / sqrt(a);
+    double y = (double)rsqrtf((float)a);
+    const double h = 0.5 * a;
+    y = y * fma(-h * y, y, 1.5);
+    y = y * fma(-h * y, y, 1.5);
+    return y;
+}
+
+// 1/a in FP64 the same way: FP32 reciprocal seed, Newton-Raphson for
+// f(y) = 1/y - a, y <- y (2 - a y), two steps. Outside FP32's normal range: 1 / a.
+__device__ __forceinline__ double rcp_fp64(double a) {
+    const double m = fabs(a);
+    if (!(m > 1e-30 && m < 1e30)) return 1.0 / a;
+    double y = (double)__frcp_rn((float)a);
+    y = y * fma(-a, y, 2.0);
+    y = y * fma(-a, y, 2.0);
+    return y;
+}
+
 // Unitary rotation G = [[cx, cy], [-conj(cy), conj(cx)]] with G [x; y] = [n; 0],
-// cx = conj(x)/n, cy = conj(y)/n, n = sqrt(|x|^2 + |y|^2): one square root and one
-// reciprocal (FP64 divide and sqrt are long sequences on this GPU).
+// cx = conj(x)/n, cy = conj(y)/n, n = sqrt(|x|^2 + |y|^2): one reciprocal square
+// root. (One thread forms it: FP64 issue, not the barriers around it, bounds
+// this solver, and every warp forming it would quadruple that work.)
 __device__ __forceinline__ void givens(double2 x, double2 y, double2& cx, double2& cy) {
     const double n2 = cabs2(x) + cabs2(y);
     if (n2 == 0.0) { cx = cone(); cy = czero(); return; }
-    const double inv = 1.0 / sqrt(n2);
+    const double inv = rsqrt_fp64(n2);
     cx = inv * conj_(x);
     cy = inv * conj_(y);
 }
@@ -252,7 +279,7 @@ __device__ void eigvecs(const double2* T, const double2* Q, int n, int lda, cons
                 for (int l = j + 1; l <= k; ++l) sacc = sacc + T[j * lda + l] * w[l];
                 double2 d = T[j * lda + j] - lam;
                 if (cabs1(d) < smin) d = make_double2(smin, 0.0);
-                w[j] = -((1.0 / cabs2(d)) * (sacc * conj_(d)));
+                w[j] = -(rcp_fp64(cabs2(d)) * (sacc * conj_(d)));
                 if (cabs1(w[j]) > 1e150) {
                     for (int l = j; l <= k; ++l) w[l] = 1e-150 * w[l];
                 }
@@ -263,7 +290,7 @@ __device__ void eigvecs(const double2* T, const double2* Q, int n, int lda, cons
                 for (int l = k; l < j; ++l) sacc = sacc + w[l] * T[l * lda + j];
                 double2 d = T[j * lda + j] - lam;
                 if (cabs1(d) < smin) d = make_double2(smin, 0.0);
-                w[j] = -((1.0 / cabs2(d)) * (sacc * conj_(d)));
+                w[j] = -(rcp_fp64(cabs2(d)) * (sacc * conj_(d)));
                 if (cabs1(w[j]) > 1e150) {
                     for (int l = k; l <= j; ++l) w[l] = 1e-150 * w[l];
                 }

@@ -62,6 +62,34 @@ def test_schur_operator_pair_hook(prec, tol):
         assert abs(sig[i] - np.vdot(ph[i], ref)) <= 10 * tol * np.linalg.norm(ph[i]) * np.linalg.norm(ref)
 
 
+def test_schur_pair_full_size_batch():
+    """The launch configuration of the benchmark's even-odd arm: 24^3x64, a batch
+    of 8 slots. Slots 0 and 7 hold independent random half fields, compared with
+    the oracle's A_hat and A_hat^+ element by element (FP32: 2e-6) with sigma;
+    slots 1..6 hold complex multiples of slot 0's fields, whose outputs must be
+    the same multiples."""
+    w, links, op, eo = eo_problem("24^3x64")
+    from paper_0911_2285_gb300 import Solver
+    p0, p7, h0, h7 = rnd(eo.n, 31), rnd(eo.n, 37), rnd(eo.n, 51), rnd(eo.n, 57)
+    c = np.exp(1j * np.arange(1, 7)) * np.arange(2, 8) / 4.0
+    p = np.stack([p0] + [ci * p0 for ci in c] + [p7])
+    ph = np.stack([h0] + [ci * h0 for ci in c] + [h7])
+    with Solver(links, w["dims"], w["kappa"], nev=2, m=8, n1=1, tol=1e-10, precision="mixed", k_max=8,
+                evenodd=True) as s:
+        ap, ahp, sig = s.apply_pair(p, ph, 0)
+    del p, ph
+    for i, (pi, hi) in ((0, (p0, h0)), (7, (p7, h7))):
+        ref = eo.apply(pi)
+        assert rel(ap[i], ref) <= 2e-6, i
+        assert rel(ahp[i], eo.apply_dag(hi)) <= 2e-6, i
+        sref = np.vdot(hi, ref)
+        assert abs(sig[i] - sref) <= 1e-5 * abs(sref), i
+    for j, ci in enumerate(c, start=1):
+        assert rel(ap[j], ci * ap[0]) <= 1e-6, j
+        assert rel(ahp[j], ci * ahp[0]) <= 1e-6, j
+        assert abs(sig[j] - abs(ci) ** 2 * sig[0]) <= 1e-5 * abs(ci) ** 2 * abs(sig[0]), j
+
+
 def test_schur_bicg_fp64_matches_oracle_and_beats_the_full_system():
     s, op, eo, w = eo_solver("4^4")
     b = workload_source("4^4", 0)
