@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "../../include/lqcd.h"
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace lqcd {
@@ -233,6 +234,209 @@ __device__ int schur(double2* A, double2* Q, int n, int lda, double2* v /* n */,
     return fail;
 }
 
+// ---------------------------------------------------------------------------
+// The same reduction in double-float arithmetic (pairs of FP32 numbers, about
+// 48 significant bits; Knuth's two-sum and Dekker's FMA two-product, as for the
+// reliable-update residual), for the restart's eigen-solves of H^(m) and
+// H^(m-1): the FP32 pipeline issues 64 times faster than FP64 on this GPU, and
+// the Householder and QR updates are the bulk of the solve. A and Q keep their
+// 16-byte slots (one double2 or one double-float complex); the scalars of a
+// step (norms, shift, rotation) are formed by one thread in FP64. On return A,
+// Q hold T and the Schur vectors in FP64 again.
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    const float h = p + e;
+    return {h, e - (h - p)};
+}
+__device__ __forceinline__ dfc dc_mul(dfc a, dfc b) {
+    return {df_mul(a.x, b.x) - df_mul(a.y, b.y), df_mul(a.x, b.y) + df_mul(a.y, b.x)};
+}
+__device__ __forceinline__ dfc dc_conj(dfc a) { return {a.x, -a.y}; }
+__device__ __forceinline__ dfc dc_scale(dfl s, dfc a) { return {df_mul(s, a.x), df_mul(s, a.y)}; }
+__device__ __forceinline__ dfl dc_abs2(dfc a) { return df_mul(a.x, a.x) + df_mul(a.y, a.y); }
+__device__ __forceinline__ float dc_abs1f(dfc a) { return fabsf(a.x.h) + fabsf(a.y.h); }
+__device__ __forceinline__ dfc dc_from(double2 a) { return {df_split(a.x), df_split(a.y)}; }
+__device__ __forceinline__ double2 dc_to(dfc a) { return make_double2(df_value(a.x), df_value(a.y)); }
+__device__ __forceinline__ dfc dc_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+__device__ __forceinline__ dfc dc_one() { return {{1.f, 0.f}, {0.f, 0.f}}; }
+
+constexpr float EPS_DF = 1.4e-14f;   // about four units of double-float rounding
+
+__device__ int schur_df(double2* A64, double2* Q64, int n, int lda, double2* v64, double* sh) {
+    const int tid = threadIdx.x;
+    dfc* A = reinterpret_cast<dfc*>(A64);
+    dfc* Q = reinterpret_cast<dfc*>(Q64);
+    dfc* v = reinterpret_cast<dfc*>(v64);
+    for (int e = tid; e < n * lda; e += blockDim.x) {   // in place: each thread converts its own slots
+        if (e % lda < n) {
+            const double2 a = A64[e];
+            A[e] = dc_from(a);
+        }
+        Q[e] = ((e / lda) == (e % lda)) ? dc_one() : dc_zero();
+    }
+    __syncthreads();
+    // Householder reduction (columns already Hessenberg skipped, reflections up
+    // to the column's last nonzero), as in schur().
+    for (int k = 0; k + 2 < n; ++k) {
+        if (tid == 0) {
+            dfl nrm2 = {0.f, 0.f}, tail = {0.f, 0.f};
+            int last = k + 1;
+            for (int i = k + 1; i < n; ++i) {
+                const dfl a2 = dc_abs2(A[i * lda + k]);
+                nrm2 = nrm2 + a2;
+                if (i >= k + 2) tail = tail + a2;
+                if (a2.h != 0.f) last = i;
+            }
+            const double alpha = sqrt(df_value(nrm2));
+            const double2 x0 = dc_to(A[(k + 1) * lda + k]);
+            const double ax0 = cabs_(x0);
+            const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+            sh[0] = tail.h > 0.f ? alpha : 0.0;   // 0: skip the step
+            sh[1] = alpha > 0.0 ? 1.0 / (alpha * (alpha + ax0)) : 0.0;
+            sh[2] = ph.x; sh[3] = ph.y;
+            sh[5] = (double)last;
+        }
+        __syncthreads();
+        const double alpha = sh[0];
+        const dfl tau = df_split(sh[1]);
+        const double2 ph = make_double2(sh[2], sh[3]);
+        const int last = (int)sh[5];
+        if (alpha == 0.0) { __syncthreads(); continue; }
+        for (int i = k + 1 + tid; i <= last; i += blockDim.x) v[i - k - 1] = A[i * lda + k];
+        __syncthreads();
+        if (tid == 0) v[0] = v[0] + dc_from(make_double2(alpha * ph.x, alpha * ph.y));
+        __syncthreads();
+        const int len = last - k;
+        for (int j = k + tid; j < n; j += blockDim.x) {
+            dfc w = dc_zero();
+            for (int i = 0; i < len; ++i) w = w + dc_mul(dc_conj(v[i]), A[(k + 1 + i) * lda + j]);
+            w = dc_scale(tau, w);
+            for (int i = 0; i < len; ++i) A[(k + 1 + i) * lda + j] = A[(k + 1 + i) * lda + j] - dc_mul(v[i], w);
+        }
+        __syncthreads();
+        for (int i = tid; i < 2 * n; i += blockDim.x) {
+            dfc* row = i < n ? A + i * lda : Q + (i - n) * lda;
+            dfc u = dc_zero();
+            for (int l = 0; l < len; ++l) u = u + dc_mul(row[k + 1 + l], v[l]);
+            u = dc_scale(tau, u);
+            for (int l = 0; l < len; ++l) row[k + 1 + l] = row[k + 1 + l] - dc_mul(u, dc_conj(v[l]));
+        }
+        __syncthreads();
+        for (int i = k + 2 + tid; i <= last; i += blockDim.x) A[i * lda + k] = dc_zero();
+        __syncthreads();
+    }
+    if (tid == 0) {
+        dfl f = {0.f, 0.f};
+        for (int i = 0; i < n; ++i)
+            for (int j = (i > 0 ? i - 1 : 0); j < n; ++j) f = f + dc_abs2(A[i * lda + j]);
+        sh[4] = sqrt(df_value(f));
+    }
+    __syncthreads();
+    const float anorm = sh[4] > 0.0 ? (float)sh[4] : 1.f;
+    __shared__ int s_l, s_hi, s_fail;
+    __shared__ dfc s_cx, s_cy, s_mu;
+    if (tid == 0) { s_hi = n - 1; s_fail = 0; }
+    __syncthreads();
+    int iters = 0, total = 0;
+    while (true) {
+        if (tid == 0) {
+            const int hi = s_hi;
+            int l = hi;
+            while (l > 0) {
+                float tst = dc_abs1f(A[(l - 1) * lda + l - 1]) + dc_abs1f(A[l * lda + l]);
+                if (tst == 0.f) tst = anorm;
+                if (dc_abs1f(A[l * lda + l - 1]) <= EPS_DF * tst) { A[l * lda + l - 1] = dc_zero(); break; }
+                --l;
+            }
+            s_l = l;
+        }
+        __syncthreads();
+        const int hi = s_hi, l = s_l;
+        if (hi <= 0) break;
+        if (l == hi) {
+            __syncthreads();
+            if (tid == 0) s_hi = hi - 1;
+            iters = 0;
+            __syncthreads();
+            continue;
+        }
+        ++iters; ++total;
+        if (iters > 60 || total > 60 * n) { if (tid == 0) s_fail = 1; __syncthreads(); break; }
+        if (tid == 0) {   // Wilkinson shift in FP64
+            const double2 a = dc_to(A[(hi - 1) * lda + hi - 1]), b = dc_to(A[(hi - 1) * lda + hi]);
+            const double2 c = dc_to(A[hi * lda + hi - 1]), d = dc_to(A[hi * lda + hi]);
+            double2 mu;
+            if (iters % 11 == 10) {
+                mu = d + make_double2(0.75 * cabs1(c), 0.0);
+            } else {
+                const double2 t = 0.5 * (a - d);
+                const double2 bc = b * c;
+                const double2 disc2 = t * t + bc;
+                const double r = cabs_(disc2);
+                const double sx = sqrt(0.5 * (r + disc2.x));
+                double sy = sqrt(0.5 * (r - disc2.x));
+                if (disc2.y < 0) sy = -sy;
+                const double2 disc = make_double2(sx, sy);
+                const double2 den1 = t + disc, den2 = t - disc;
+                const double2 den = cabs2(den1) >= cabs2(den2) ? den1 : den2;
+                mu = cabs2(den) > 0.0 ? d - cdiv(bc, den) : d;
+            }
+            s_mu = dc_from(mu);
+        }
+        __syncthreads();
+        const dfc mu = s_mu;
+        for (int k = l; k < hi; ++k) {
+            if (tid == 0) {
+                dfc x, y;
+                if (k == l) { x = A[l * lda + l] - mu; y = A[(l + 1) * lda + l]; }
+                else { x = A[k * lda + k - 1]; y = A[(k + 1) * lda + k - 1]; }
+                const double n2 = df_value(dc_abs2(x) + dc_abs2(y));
+                if (n2 == 0.0) { s_cx = dc_one(); s_cy = dc_zero(); }
+                else {
+                    const dfl inv = df_split(rsqrt_fp64(n2));
+                    s_cx = dc_scale(inv, dc_conj(x));
+                    s_cy = dc_scale(inv, dc_conj(y));
+                }
+            }
+            __syncthreads();
+            const dfc cx = s_cx, cy = s_cy;
+            const dfc cxc = dc_conj(cx), cyc = dc_conj(cy);
+            const int j0 = (k == l) ? l : k - 1;
+            for (int j = j0 + tid; j < n; j += blockDim.x) {
+                const dfc a = A[k * lda + j], b = A[(k + 1) * lda + j];
+                A[k * lda + j] = dc_mul(cx, a) + dc_mul(cy, b);
+                A[(k + 1) * lda + j] = dc_mul(cxc, b) - dc_mul(cyc, a);
+            }
+            __syncthreads();
+            const int i1 = min(k + 2, hi);
+            for (int i = tid; i < (i1 + 1) + n; i += blockDim.x) {
+                dfc* row = i <= i1 ? A + i * lda : Q + (i - i1 - 1) * lda;
+                const dfc a = row[k], b = row[k + 1];
+                row[k] = dc_mul(a, cxc) + dc_mul(b, cyc);
+                row[k + 1] = dc_mul(b, cx) - dc_mul(a, cy);
+            }
+            __syncthreads();
+            if (k > l && tid == 0) A[(k + 1) * lda + k - 1] = dc_zero();
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    const int fail = s_fail;
+    for (int e = tid; e < n * lda; e += blockDim.x) {   // back to FP64, in place
+        if (e % lda < n) {
+            const dfc a = A[e];
+            A64[e] = dc_to(a);
+        }
+        const dfc q = Q[e];
+        Q64[e] = dc_to(q);
+    }
+    __syncthreads();
+    return fail;
+}
+
 // Order of the eigenvalues on the diagonal of T: smallest |lambda|, then Im.
 __device__ void order_eigs(const double2* T, int n, int lda, int* ord) {
     if (threadIdx.x == 0) {
@@ -338,8 +542,9 @@ __device__ void eigvecs(const double2* T, const double2* Q, int n, int lda, cons
 // Full eigen-solve of the n x n matrix in A (shared). Outputs sorted
 // eigenvalues to lam (n), and vectors for the first nsel.
 __device__ int eig_block(double2* A, double2* Q, int n, int lda, int nsel, double2* lam, double2* Y,
-                         double2* Z, int ldyz, double2* W1, double2* W2, double2* v, double* sh, int* ord) {
-    int fail = schur(A, Q, n, lda, v, sh);
+                         double2* Z, int ldyz, double2* W1, double2* W2, double2* v, double* sh, int* ord,
+                         bool dfloat = false) {
+    int fail = dfloat ? schur_df(A, Q, n, lda, v, sh) : schur(A, Q, n, lda, v, sh);
     double anorm = sh[4];
     order_eigs(A, n, lda, ord);
     for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = A[ord[i] * lda + ord[i]];
@@ -405,7 +610,7 @@ __device__ int restart_eigs_part(const double2* H, int ldh, int m, int nev, int 
     __syncthreads();
     double2* scratch = which ? Wk.W2 : Wk.W1;   // 2 n nev <= m^2
     int fail = eig_block(S.A, S.Q, n, n, nev, which ? Wk.lamtmp2 : Wk.lamtmp, which ? Wk.y2 : Wk.y1,
-                         which ? Wk.z2 : Wk.z1, nev, scratch, scratch + (size_t)n * nev, S.v, S.sh, S.ord);
+                         which ? Wk.z2 : Wk.z1, nev, scratch, scratch + (size_t)n * nev, S.v, S.sh, S.ord, true);
     if (which)
         for (int i = tid; i < nev; i += blockDim.x) { Wk.y2[(m - 1) * nev + i] = czero(); Wk.z2[(m - 1) * nev + i] = czero(); }
     __syncthreads();
