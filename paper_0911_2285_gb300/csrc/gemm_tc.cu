@@ -39,28 +39,34 @@ namespace {
 
 constexpr int TC_KT = 32;        // reals per row per K-tile (128 bytes)
 constexpr int TC_M = 128;        // X rows per CTA tile
-constexpr int TC_NB = 8;         // Y fields per launch (N = 2 * TC_NB)
+constexpr int TC_NB = 8;         // Y fields per launch, narrow form (N = 2 * TC_NB)
+constexpr int TC_NB_WIDE = 24;   // wide form (N = 48): one launch serves up to 24 Y fields, so X is
+                                 // read once and each MMA instruction does three times the work
 constexpr int TC_STAGES = 5;
 constexpr int TC_FLUSH = 2;      // K-tiles per FP32 accumulation run in tensor memory
 constexpr int TC_XW = 8;         // split (transform) warps
 constexpr int TC_THREADS = 32 * (2 + TC_XW);
 constexpr int TC_NBUF = 4;       // accumulator sets in flight (runs the readers may lag behind)
 constexpr int TC_SUPER = 16;     // runs summed in FP32 before an FP64 add
-constexpr unsigned TC_TMEM_COLS = 128;  // TC_NBUF runs x (big.big, correction) x 16 columns
+// tensor-memory columns: TC_NBUF runs x (big.big, correction) x 2 NB columns, as a power of two
+__host__ __device__ constexpr unsigned tc_tmem_cols(int nb) {
+    return (unsigned)(TC_NBUF * 2 * 2 * nb) <= 128u ? 128u : (unsigned)(TC_NBUF * 2 * 2 * nb) <= 256u ? 256u : 512u;
+}
 
-struct __align__(1024) TcStage {
+template <int NB> struct __align__(1024) TcStage {
     float xa[TC_M * TC_KT];      // TMA X tile, then its TF32 big part in place
     float xs[TC_M * TC_KT];      // small part of X
-    float yb[2 * TC_NB * TC_KT]; // rows 0-7: TMA Y tile -> big part; rows 8-15: big part of Z
-    float ys[2 * TC_NB * TC_KT]; // small parts of Y and Z
+    float yb[2 * NB * TC_KT];    // rows 0..NB-1: TMA Y tile -> big part; rows NB..2NB-1: big part of Z
+    float ys[2 * NB * TC_KT];    // small parts of Y and Z
 };
-static_assert(sizeof(TcStage) % 1024 == 0, "stage must keep 1024-byte alignment");
+static_assert(sizeof(TcStage<TC_NB>) % 1024 == 0, "stage must keep 1024-byte alignment");
+static_assert(sizeof(TcStage<TC_NB_WIDE>) % 1024 == 0, "stage must keep 1024-byte alignment");
 struct TcBars {
     uint64_t full[TC_STAGES], ready[TC_STAGES], empty[TC_STAGES], accfull[TC_NBUF], accempty[TC_NBUF];
     unsigned tmem;
     int abort;
 };
-constexpr size_t TC_SMEM = TC_STAGES * sizeof(TcStage) + 1024 /*align slack*/ + sizeof(TcBars);
+template <int NB> constexpr size_t tc_smem() { return TC_STAGES * sizeof(TcStage<NB>) + 1024 /*align slack*/ + sizeof(TcBars); }
 
 __device__ __forceinline__ void split4(float4 v, float4& big, float4& small) {
     big = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
@@ -84,11 +90,16 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, unsigned parity, vo
 // TF32 big/small parts, and warps 2-5 (one per tensor-memory lane quarter)
 // also move each finished accumulation run into their FP64 sums.
 // Grid (split-K CTAs, row tiles of 128). part: [gridDim.y][gridDim.x][128][16] FP64.
+// NB: Y fields per launch (N = 2 NB columns: the Y fields and their Z twins).
+template <int NB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     dots_tc_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap my, int box_rows,
                    long long tiles, double* part, int* err) {
+    constexpr int NC = 2 * NB;                       // accumulator columns
+    constexpr unsigned TMEM_COLS = tc_tmem_cols(NB);
     extern __shared__ unsigned char smem_raw[];
-    TcStage* st = reinterpret_cast<TcStage*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    using Stage = TcStage<NB>;
+    Stage* st = reinterpret_cast<Stage*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     TcBars* B = reinterpret_cast<TcBars*>(st + TC_STAGES);
     volatile int* abort = &B->abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -97,7 +108,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const long long t1 = (long long)(blockIdx.x + 1) * tiles / gridDim.x;
     const int n = (int)(t1 - t0);
     const int ngroups = (n + TC_FLUSH - 1) / TC_FLUSH;
-    const unsigned tx = (unsigned)(box_rows + TC_NB) * TC_KT * 4;
+    const unsigned tx = (unsigned)(box_rows + NB) * TC_KT * 4;
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -111,7 +122,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (warp == 0) {
         __syncwarp();
-        tmem_alloc(&B->tmem, TC_TMEM_COLS);
+        tmem_alloc(&B->tmem, TMEM_COLS);
         tmem_relinquish();
     }
     if (warp >= 2) {   // rows the TMA box does not cover stay zero in both X buffers
@@ -126,11 +137,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = B->tmem;
-    constexpr unsigned IDESC = idesc_tf32(TC_M, 2 * TC_NB);
+    constexpr unsigned IDESC = idesc_tf32(TC_M, NC);
 
-    double acc[16];
+    double acc[NC];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
 
     if (warp == 0) {
         if (lane == 0) {   // ---------------- TMA producer
@@ -159,11 +170,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 if (!wait_or_abort(&B->ready[s], (unsigned)(i / TC_STAGES) & 1u, abort)) break;
                 tc_fence_after();
-                TcStage& S = st[s];
+                Stage& S = st[s];
                 // big.big and the two correction products go to separate accumulators
                 // (the tensor core truncates as it accumulates: keeping the small
                 // terms apart and the runs short keeps the sum at FP32 accuracy)
-                const unsigned dm = tmem + (unsigned)(b * 32), dc = dm + 16;
+                const unsigned dm = tmem + (unsigned)(b * 2 * NC), dc = dm + NC;
 #pragma unroll
                 for (int kk = 0; kk < TC_KT / 8; ++kk) {   // K = 8 reals (32 bytes) per MMA
                     const uint64_t ab = sdesc_k128(S.xa + 8 * kk), as = sdesc_k128(S.xs + 8 * kk);
@@ -184,26 +195,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const bool reader = warp < 6;
         const unsigned lane_base = (unsigned)((warp & 3) * 32) << 16;
         int next_group = 0;
-        float sum32[16];   // FP32 sum of up to TC_SUPER runs (FP64 adds are slow on this GPU)
+        float sum32[NC];   // FP32 sum of up to TC_SUPER runs (FP64 adds are slow on this GPU)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) sum32[c] = 0.f;
+        for (int c = 0; c < NC; ++c) sum32[c] = 0.f;
         auto read_group = [&](int g) -> bool {
             const int b = g % TC_NBUF;
             // warp-uniform outcome: tcgen05.ld below needs the whole warp
             if (!__all_sync(0xffffffffu, wait_or_abort(&B->accfull[b], (unsigned)(g / TC_NBUF) & 1u, abort)))
                 return false;
             tc_fence_after();
-            float v[16], w[16];
-            tmem_ld16(tmem + lane_base + (unsigned)(b * 32), v);
-            tmem_ld16(tmem + lane_base + (unsigned)(b * 32 + 16), w);
+#pragma unroll
+            for (int c0 = 0; c0 < NC; c0 += 16) {
+                float v[16], w[16];
+                tmem_ld16(tmem + lane_base + (unsigned)(b * 2 * NC + c0), v);
+                tmem_ld16(tmem + lane_base + (unsigned)(b * 2 * NC + NC + c0), w);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) sum32[c0 + c] += v[c] + w[c];
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&B->accempty[b]);
-#pragma unroll
-            for (int c = 0; c < 16; ++c) sum32[c] += v[c] + w[c];
             if (g % TC_SUPER == TC_SUPER - 1 || g == ngroups - 1) {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
+                for (int c = 0; c < NC; ++c) {
                     acc[c] += (double)sum32[c];
                     sum32[c] = 0.f;
                 }
@@ -217,7 +231,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ok = false;
                 break;
             }
-            TcStage& S = st[s];
+            Stage& S = st[s];
             float4* xa = reinterpret_cast<float4*>(S.xa);
             float4* xs = reinterpret_cast<float4*>(S.xs);
             for (int p = xt; p < box_rows * TC_KT / 4; p += 32 * TC_XW) {
@@ -226,17 +240,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 xa[p] = big;
                 xs[p] = small;
             }
-            if (xt < TC_NB * TC_KT / 4) {   // Y and its Z twin
+            for (int yt = xt; yt < NB * TC_KT / 4; yt += 32 * TC_XW) {   // Y and its Z twin
                 float4* yb = reinterpret_cast<float4*>(S.yb);
                 float4* ys = reinterpret_cast<float4*>(S.ys);
-                const float4 y = yb[xt];
+                const float4 y = yb[yt];
                 float4 big, small;
                 split4(y, big, small);
-                yb[xt] = big;
-                ys[xt] = small;
+                yb[yt] = big;
+                ys[yt] = small;
                 split4(make_float4(y.y, -y.x, y.w, -y.z), big, small);
-                yb[TC_NB * TC_KT / 4 + xt] = big;
-                ys[TC_NB * TC_KT / 4 + xt] = small;
+                yb[NB * TC_KT / 4 + yt] = big;
+                ys[NB * TC_KT / 4 + yt] = small;
             }
             fence_proxy_async();
             __syncwarp();
@@ -248,9 +262,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             while (ok && next_group < ngroups) ok = read_group(next_group++);
         if (ok && reader) {
             const int r = (warp & 3) * 32 + lane;
-            double* out = part + (((size_t)blockIdx.y * gridDim.x + blockIdx.x) * TC_M + r) * 16;
+            double* out = part + (((size_t)blockIdx.y * gridDim.x + blockIdx.x) * TC_M + r) * NC;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) out[c] = acc[c];
+            for (int c = 0; c < NC; ++c) out[c] = acc[c];
         }
     }
     tc_fence_before();
@@ -259,21 +273,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) {
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem, TC_TMEM_COLS);
+        tmem_dealloc(tmem, TMEM_COLS);
     }
 }
 
 // C[i][j] (or conj into C[j][i]) = sum over the split-K partials, FP64.
-__global__ void dots_tc_reduce_kernel(int a, int b, int nblk, const double* part, double2* Cm, int ldc,
+__global__ void dots_tc_reduce_kernel(int a, int b, int nb, int nblk, const double* part, double2* Cm, int ldc,
                                       int conj_store) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= a * b) return;
     const int i = q / b, j = q % b, ty = i / TC_M, r = i % TC_M;
     double re = 0.0, im = 0.0;
     for (int k = 0; k < nblk; ++k) {
-        const double* p = part + (((size_t)ty * nblk + k) * TC_M + r) * 16;
+        const double* p = part + (((size_t)ty * nblk + k) * TC_M + r) * (2 * nb);
         re += p[j];
-        im += p[TC_NB + j];
+        im += p[nb + j];
     }
     if (conj_store) Cm[(size_t)j * ldc + i] = make_double2(re, -im);
     else Cm[(size_t)i * ldc + j] = make_double2(re, im);
@@ -610,12 +624,18 @@ bool dots_tc_supported(int a, const void* X, const void* Y, size_t N) {
            ((uintptr_t)Y & 15) == 0 && get_encode() == cudaSuccess;
 }
 
-size_t dots_tc_scratch_doubles(int a) { return (size_t)((a + TC_M - 1) / TC_M) * num_sms() * TC_M * 16; }
+size_t dots_tc_scratch_doubles(int a) {
+    return (size_t)((a + TC_M - 1) / TC_M) * num_sms() * TC_M * 2 * TC_NB_WIDE;
+}
 
 cudaError_t prepare_dots_tc() {
     std::call_once(g_prepare_once, [] {
-        g_prepare_err = cudaFuncSetAttribute((const void*)dots_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)TC_SMEM);
+        g_prepare_err = cudaFuncSetAttribute((const void*)dots_tc_kernel<TC_NB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<TC_NB>());
+        if (g_prepare_err == cudaSuccess)
+            g_prepare_err = cudaFuncSetAttribute((const void*)dots_tc_kernel<TC_NB_WIDE>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)tc_smem<TC_NB_WIDE>());
         if (g_prepare_err == cudaSuccess)
             g_prepare_err = cudaFuncSetAttribute((const void*)restart_tc_kernel,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM);
@@ -666,22 +686,30 @@ cudaError_t launch_dots_tc(int a, const void* X, size_t x_stride, int b, const v
     const int ty = (a + TC_M - 1) / TC_M;
     int nblk = num_sms();
     if (nblk > tiles) nblk = (int)tiles;
-    if ((size_t)ty * nblk * TC_M * 16 > scratch_doubles) return cudaErrorInvalidValue;
+    // up to 8 Y fields per launch in the narrow form (N = 16), more in the wide one
+    // (N = 48), which reads X once for 24 fields
+    const int nb = b > TC_NB ? TC_NB_WIDE : TC_NB;
+    if ((size_t)ty * nblk * TC_M * 2 * nb > scratch_doubles) return cudaErrorInvalidValue;
     const int box_rows = ty > 1 ? TC_M : (a + 7) / 8 * 8;
     CUtensorMap mx;
     if (!encode_rows(&mx, X, N, a, x_stride, box_rows)) return cudaErrorInvalidValue;
-    for (int j0 = 0; j0 < b; j0 += TC_NB) {
-        const int bb = b - j0 < TC_NB ? b - j0 : TC_NB;
+    for (int j0 = 0; j0 < b; j0 += nb) {
+        const int bb = b - j0 < nb ? b - j0 : nb;
         CUtensorMap my;
         const char* Yj = reinterpret_cast<const char*>(Y) + (size_t)j0 * y_stride;
-        if (!encode_rows(&my, Yj, N, bb, y_stride, TC_NB)) return cudaErrorInvalidValue;
-        dots_tc_kernel<<<dim3(nblk, ty), TC_THREADS, TC_SMEM, st>>>(mx, my, box_rows, tiles, scratch, err);
+        if (!encode_rows(&my, Yj, N, bb, y_stride, nb)) return cudaErrorInvalidValue;
+        if (nb == TC_NB)
+            dots_tc_kernel<TC_NB><<<dim3(nblk, ty), TC_THREADS, tc_smem<TC_NB>(), st>>>(mx, my, box_rows, tiles,
+                                                                                     scratch, err);
+        else
+            dots_tc_kernel<TC_NB_WIDE><<<dim3(nblk, ty), TC_THREADS, tc_smem<TC_NB_WIDE>(), st>>>(
+                mx, my, box_rows, tiles, scratch, err);
         count_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         double2* Cj = conj_store ? Cm + (size_t)j0 * ldc : Cm + j0;
-        dots_tc_reduce_kernel<<<(int)(((size_t)a * bb + 127) / 128), 128, 0, st>>>(a, bb, nblk, scratch, Cj, ldc,
-                                                                            conj_store);
+        dots_tc_reduce_kernel<<<(int)(((size_t)a * bb + 127) / 128), 128, 0, st>>>(a, bb, nb, nblk, scratch, Cj,
+                                                                            ldc, conj_store);
         count_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
