@@ -572,15 +572,11 @@ def main_ours(args):
         "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload} Wilson-Dirac, random SU(3) links eps={w['eps']}, "
-                               f"kappa={w['kappa']}, {n_rhs} Z2 sources; Incremental eigBiCG (eigBiCG on "
-                               f"{n1} sources, nev={w['nev']} m={w['m']}, then deflated BiCG), autotuned "
-                               f"batches of {k}, "
-                               f"FP32 Krylov + FP64 reliable updates, tol 1e-10",
-                   "dims": list(w["dims"]), "n_rhs": n_rhs, "n1": n1, "nev": w["nev"], "m": w["m"],
-                   "k": k, "k_autotune_ms_per_iteration": {str(kk): batch_ms[kk] for kk in (1, 2, 4, 8)}
-                   if batch_ms else None, "precision": "mixed", "parallelism": f"independent jobs x{world}",
-                   "l2": "inputs larger than L2 (each step streams GBs of fields)"},
+        "config": dict(workload_config(args.workload, w, n_rhs, n1, world),
+                       method=f"GPU: autotuned batches of {k}, FP32 Krylov vectors and links with FP64 "
+                              f"reliable updates, CUDA-graph iteration chunks",
+                       k=k, k_autotune_ms_per_iteration={str(kk): batch_ms[kk] for kk in (1, 2, 4, 8)}
+                       if batch_ms else None, precision="mixed"),
         "e2e": e2e,
         "gpu_launches": launches,
         "iters_per_rhs": {"eigbicg": it_eig, "deflated": it_def, "matvecs_per_rhs": mv_per_rhs},
@@ -658,6 +654,17 @@ def w_default(name):
     return WORKLOADS[name]["n_rhs"]
 
 
+def workload_config(name, w, n_rhs, n1, world):
+    """The workload both arms report: the problem, its sizes and the Incremental
+    eigBiCG parameters."""
+    return {"workload": f"{name} Wilson-Dirac, random SU(3) links eps={w['eps']}, kappa={w['kappa']}, "
+                        f"{n_rhs} Z2 sources to FP64 residual 1e-10; Incremental eigBiCG (eigBiCG on {n1} "
+                        f"sources, nev={w['nev']} m={w['m']}, then deflated BiCG)",
+            "dims": list(w["dims"]), "n_rhs": n_rhs, "n1": n1, "nev": w["nev"], "m": w["m"],
+            "parallelism": f"independent jobs x{world}",
+            "l2": "inputs larger than L2 (each step streams GBs of fields)"}
+
+
 def main_reference(args):
     """The CPU oracle on the same workload, on all host cores: each step is one oracle BiCG
     iteration on the full field in each of one single-threaded process per core (independent
@@ -670,6 +677,7 @@ def main_reference(args):
     from seeded_inputs import WORKLOADS, workload_links
     w = dict(WORKLOADS[args.workload])
     links = workload_links(args.workload)
+    n_rhs = args.n_rhs or w_default(args.workload)
     iters = REF_ITERS.get(args.workload, 120)
     procs, model = host_cores()
     rates, times = [], []
@@ -686,7 +694,9 @@ def main_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload} Wilson-Dirac, kappa={w['kappa']}", "dims": list(w["dims"])},
+        "config": dict(workload_config(args.workload, w, n_rhs, min(w["n1"], n_rhs), 1),
+                       method="CPU oracle: plain FP64 BiCG (numpy), one iteration per process and step, "
+                              "scaled by the BiCG iteration count"),
         "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": procs, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
