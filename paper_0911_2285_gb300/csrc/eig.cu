@@ -807,9 +807,19 @@ __global__ void __launch_bounds__(ET) restart_slots_kernel(SlotState* states, co
 }
 
 // Final Ritz pairs of a window: eig(H^(vs)), nev smallest, scales folded.
-__global__ void __launch_bounds__(ET) final_ritz_kernel(SlotState* states, const SlotPtrs* ptrs, int slot,
+// Block j: slot slot0 + j, outputs at Yc + j ostride, Zc + j ostride, lam + j lstride,
+// nout[j], work area work + j wstride (the windows' final Ritz pairs of several
+// slots at once: each depends only on its own window).
+__global__ void __launch_bounds__(ET) final_ritz_kernel(SlotState* states, const SlotPtrs* ptrs, int slot0,
                                                         double2* Yc, double2* Zc, double2* lam, int* nout,
-                                                        double2* work) {
+                                                        double2* work, size_t ostride, size_t lstride,
+                                                        size_t wstride) {
+    const int slot = slot0 + blockIdx.x;
+    Yc += blockIdx.x * ostride;
+    Zc += blockIdx.x * ostride;
+    lam += blockIdx.x * lstride;
+    nout += blockIdx.x;
+    work += blockIdx.x * wstride;
     const SlotState& st = states[slot];
     const SlotPtrs& P = ptrs[slot];
     const int n = st.vs, m = st.m;
@@ -1064,8 +1074,16 @@ cudaError_t launch_restart_coeffs(SlotState* states, const SlotPtrs* ptrs, int n
 
 cudaError_t launch_final_ritz(SlotState* states, const SlotPtrs* ptrs, int slot, double2* Yc, double2* Zc,
                               double2* lam, int* nout, double2* w, cudaStream_t st) {
+    return launch_final_ritz_slots(states, ptrs, slot, 1, Yc, Zc, lam, nout, 0, 0, w, st);
+}
+
+cudaError_t launch_final_ritz_slots(SlotState* states, const SlotPtrs* ptrs, int slot0, int nslots, double2* Yc,
+                                    double2* Zc, double2* lam, int* nout, size_t ostride, size_t lstride,
+                                    double2* w, cudaStream_t st) {
+    if (nslots < 1 || nslots > MAX_SLOTS) return cudaErrorInvalidValue;
     size_t sm = EigSmem::bytes(MAX_M);
-    final_ritz_kernel<<<1, ET, sm, st>>>(states, ptrs, slot, Yc, Zc, lam, nout, w);
+    final_ritz_kernel<<<nslots, ET, sm, st>>>(states, ptrs, slot0, Yc, Zc, lam, nout, w, ostride, lstride,
+                                              eig_work_elems());
     count_launches(1);
     return cudaGetLastError();
 }

@@ -189,6 +189,12 @@ cudaError_t launch_pivot_select(int n, const double2* B, int ld, double tau, int
 // coefficients Y (vs x nev) and Z into Yc/Zc with the window scales folded in.
 cudaError_t launch_final_ritz(SlotState* st_, const SlotPtrs* ptrs, int slot, double2* Yc, double2* Zc,
                               double2* lam, int* nout, double2* work, cudaStream_t st);
+// The same for slots slot0 .. slot0+nslots-1 in one launch (one block each):
+// slot slot0 + j writes Yc/Zc + j ostride, lam + j lstride, nout[j], and uses
+// the work area work + j eig_work_elems().
+cudaError_t launch_final_ritz_slots(SlotState* st_, const SlotPtrs* ptrs, int slot0, int nslots, double2* Yc,
+                                    double2* Zc, double2* lam, int* nout, size_t ostride, size_t lstride,
+                                    double2* work, cudaStream_t st);
 // Small matrix helpers: C = A B (all row-major, n x k x m), one CTA.
 cudaError_t launch_small_gemm(int n, int k, int m, const double2* A, int lda, int transA,
                               const double2* B, int ldb, double2* C, int ldc, cudaStream_t st);

@@ -46,6 +46,7 @@ void set_error(const char* what, cudaError_t e) {
 
 constexpr int CHECK_EVERY = 8;   // iterations per graph launch / status poll
 constexpr int TILED = 100;       // dslash_variant value of the plane-streaming kernel
+constexpr size_t RITZ_STRIDE = (size_t)2 * MAX_M * MAX_M + MAX_M;   // double2 per slot in ritz_all
 
 }  // namespace
 
@@ -95,6 +96,8 @@ struct lqcd_ctx {
     double2* partials = nullptr;
     unsigned* counters = nullptr;
     double2* eigwork = nullptr;     // kmax * eig_work_elems()
+    double2* ritz_all = nullptr;    // per slot: final Ritz coefficients Yc, Zc (MAX_M^2 each) and values
+    int* ritz_n = nullptr;          // per slot: number of final Ritz pairs
     double2* mdscratch = nullptr;
     size_t mdscratch_elems = 0;
     ApplyJob* d_jobs = nullptr;
@@ -403,6 +406,7 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     if (c->eo) plan += K * c->Nfull * 16 * 2 + K * c->dbytes * 3 + 2 * K * c->kbytes;
     plan += 2 * (size_t)c->n_def_max * c->kbytes;
     plan += (MAX_SLOTS * eig_work_elems() + 16) * 16 + c->mdscratch_elems * 16 + K * CNT_COUNT * PARTIAL_STRIDE * 16;
+    plan += MAX_SLOTS * RITZ_STRIDE * 16 + MAX_SLOTS * sizeof(int);
     c->plan_bytes = plan;
     c->win_bytes = (size_t)2 * (c->m + 1) * c->kbytes;
     if (c->p.hbm_budget_bytes && plan > c->p.hbm_budget_bytes) {
@@ -444,6 +448,8 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
     AL(c->partials, K * CNT_COUNT * PARTIAL_STRIDE * 16);
     AL(c->counters, K * CNT_COUNT * sizeof(unsigned));
     AL(c->eigwork, ((size_t)MAX_SLOTS * eig_work_elems() + 16) * 16);
+    AL(c->ritz_all, (size_t)MAX_SLOTS * RITZ_STRIDE * 16);
+    AL(c->ritz_n, MAX_SLOTS * sizeof(int));
     AL(c->mdscratch, c->mdscratch_elems * 16);
     AL(c->d_jobs, sizeof(ApplyJob) * 2 * K);
     AL(c->staging, K * c->Nfull * 16);
@@ -1134,7 +1140,8 @@ lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol, bool rec_s
 }
 
 // Final Ritz vectors of one finished eigBiCG slot, appended to the eigenspace.
-lqcd_status grow_slot(lqcd_ctx* c, int s) {
+// ritz_ready: the slot's final Ritz pairs are already in ritz_all (grow_from_windows).
+lqcd_status grow_slot(lqcd_ctx* c, int s, bool ritz_ready = false) {
     const SlotState& st = c->h_state[s];
     c->last_vs[s] = st.vs;
     c->last_restarts[s] = st.restarts;
@@ -1146,11 +1153,14 @@ lqcd_status grow_slot(lqcd_ctx* c, int s) {
     const int room = c->n_def_max - c->n_def;
     if (room <= 0) return LQCD_OK;
     const int take = std::min(nsel, room);
-    double2* Yc = c->dsmall + (size_t)MAX_SMALL * MAX_SMALL * 2;
+    // this slot's final Ritz pairs, formed for every slot of the batch at once
+    // (grow_from_windows)
+    double2* Yc = c->ritz_all + (size_t)s * RITZ_STRIDE;
     double2* Zc = Yc + (size_t)MAX_M * MAX_M;
     double2* lam = Zc + (size_t)MAX_M * MAX_M;
-    int* nout = c->dinfo + 8;
-    CK(launch_final_ritz(c->d_state, c->d_ptrs, s, Yc, Zc, lam, nout, c->eigwork, c->stream));
+    if (!ritz_ready)
+        CK(launch_final_ritz_slots(c->d_state, c->d_ptrs, s, 1, Yc, Zc, lam, c->ritz_n + s, 0, 0, c->eigwork,
+                                   c->stream));
     std::vector<double2> hl(nsel);
     CK(cudaMemcpyAsync(hl.data(), lam, sizeof(double2) * nsel, cudaMemcpyDeviceToHost, c->stream));
     const SlotPtrs& P = c->h_ptrs[s];
@@ -1170,8 +1180,14 @@ lqcd_status grow_slot(lqcd_ctx* c, int s) {
 // After an eigBiCG batch: final Ritz vectors of every slot, appended in slot order.
 lqcd_status grow_from_windows(lqcd_ctx* c, int k) {
     c->last_window_valid = 1;
+    if (k > 0) {   // final Ritz pairs of every window in one launch (each depends on its window only)
+        double2* Yc = c->ritz_all;
+        CK(launch_final_ritz_slots(c->d_state, c->d_ptrs, 0, k, Yc, Yc + (size_t)MAX_M * MAX_M,
+                                   Yc + (size_t)2 * MAX_M * MAX_M, c->ritz_n, RITZ_STRIDE, RITZ_STRIDE,
+                                   c->eigwork, c->stream));
+    }
     for (int s = 0; s < k; ++s) {
-        lqcd_status r = grow_slot(c, s);
+        lqcd_status r = grow_slot(c, s, true);
         if (r != LQCD_OK) return r;
     }
     return LQCD_OK;
