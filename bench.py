@@ -486,8 +486,10 @@ def main_ours(args):
             run_job(s, b_host, x_host, n1)
         torch.cuda.synchronize()
         e2e_s = barrier_max((time.perf_counter() - t0) / args.steps, world)
+        # lqcd_solve copies every source b and its initial guess (x, zero here) to the
+        # device and the solution back
         nbytes = src.nbytes
-        e2e = {"value": weak_value(n_rhs, world, e2e_s), "unit": "RHS/s", "h2d_bytes_per_step": nbytes,
+        e2e = {"value": weak_value(n_rhs, world, e2e_s), "unit": "RHS/s", "h2d_bytes_per_step": 2 * nbytes,
                "d2h_bytes_per_step": nbytes}
         del b_host, x_host
 

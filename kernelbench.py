@@ -2,11 +2,15 @@
 the committed ncu captures).
 
     python kernelbench.py dhop --workload 16^3x32 --variants 2 4
+    python kernelbench.py eopair --workload 16^3x32
     python kernelbench.py dots --a 80 --b 8 --n 1572864
 
 ``dhop``: the operator-pair kernel shapes (A p, A^+ phat for k slots) through
 ``Solver.time_kernel``; after the timed runs each listed shape is launched once
-more (the launches an ncu capture skips to). ``dots``: the inner-product matrix
+more (the launches an ncu capture skips to). ``eopair``: the even-odd (Schur
+complement) operator pair A_hat p, A_hat^+ phat on the odd half lattice for k
+slots (two stage kernels per pair), timed reps times, then launched once more.
+``dots``: the inner-product matrix
 X^H Y of FP32 fields on the tensor cores and on the CUDA cores; the last launch
 is one more tensor-core call. ``restart``: eigBiCG on k sources stopped a few
 iterations after the first window restart (the m-th iteration launches the
@@ -32,6 +36,10 @@ def main(argv=None):
     d.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="skip the init autotuner: the only operator launches are the listed shapes' "
                         "(reps timed + 1 each, in order)")
+    e = sub.add_parser("eopair")
+    e.add_argument("--workload", default="16^3x32")
+    e.add_argument("--k", type=int, default=8)
+    e.add_argument("--reps", type=int, default=5)
     r = sub.add_parser("restart")
     r.add_argument("--workload", default="16^3x32")
     r.add_argument("--k", type=int, default=2)
@@ -61,6 +69,22 @@ def main(argv=None):
                 print(f"  shape {v}: {ms:.4f} ms  {alg / ms / 1e6:.0f} GB/s")
             for v in args.variants:
                 s.time_kernel(10 + v, args.k, 1)
+    elif args.what == "eopair":
+        from seeded_inputs import WORKLOADS, workload_links
+        w = WORKLOADS[args.workload]
+        with Solver(workload_links(args.workload), w["dims"], w["kappa"], nev=2, m=8, n1=1, tol=1e-10,
+                    maxiter=100, precision="mixed", k_max=args.k, evenodd=True) as s:
+            V = 1
+            for L in w["dims"]:
+                V *= L
+            # per stage the links once (two-row FP32); per slot, stage 1 reads p, phat and
+            # writes the two even-half intermediates, stage 2 reads them and p, phat and
+            # writes A_hat p, A_hat^+ phat: ten half-lattice fields
+            alg = 2 * V * 4 * 48 + args.k * 10 * (V // 2) * 96
+            ms = s.time_kernel(0, args.k, args.reps)
+            print(f"{args.workload}: even-odd operator pair, k={args.k}: {ms:.4f} ms, "
+                  f"algorithmic bytes {alg} ({alg / ms / 1e6:.0f} GB/s)")
+            s.time_kernel(0, args.k, 1)
     elif args.what == "restart":
         from seeded_inputs import WORKLOADS, workload_links, workload_source
         w = WORKLOADS[args.workload]
