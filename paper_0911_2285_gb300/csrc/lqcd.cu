@@ -22,11 +22,36 @@
 #include "../../include/lqcd.h"
 #include "kernels.cuh"
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define LQCD_HAVE_NVTX 1
+#endif
+
 using namespace lqcd;
 
 namespace {
 
 thread_local std::string g_last_error;
+
+// Named host range for timeline tools (Nsight Systems): the stages of a solve
+// (sources in, deflation, iterations, eigenspace growth, solutions out), the
+// autotuners and the serving calls. NVTX is inert unless a tool is attached.
+struct Range {
+    explicit Range(const char* name) {
+#ifdef LQCD_HAVE_NVTX
+        nvtxRangePushA(name);
+#else
+        (void)name;
+#endif
+    }
+    ~Range() {
+#ifdef LQCD_HAVE_NVTX
+        nvtxRangePop();
+#endif
+    }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 void set_error(const char* what, cudaError_t e) {
     char buf[512];
@@ -368,6 +393,7 @@ static lqcd_status autotune_batch(lqcd_ctx* c);
 // ============================================================== lifecycle
 extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* params, const double* links,
                                          void* cuda_stream) {
+    Range nvtx_("lqcd_eigbicg_init");
     if (!out || !links) return LQCD_ERR_ARG;
     *out = nullptr;
     lqcd_status vs = validate(params);
@@ -704,6 +730,7 @@ lqcd_status residual_fields(lqcd_ctx* c, int nf, const double2* x, double2* r, c
 // full buffers, b_hat = b_o + k D_oe b_e, x0 -> its odd half, and ||b|| of the
 // full systems for the tolerance.
 lqcd_status load_sources(lqcd_ctx* c, int s0, int k, const double* b, const double* x0, int on_device) {
+    Range nvtx_("sources to device");
     if (!c->eo) {
         lqcd_status s = upload(c, b, k, c->b_all + (size_t)s0 * c->N, 0, on_device);
         if (s != LQCD_OK) return s;
@@ -725,6 +752,7 @@ lqcd_status load_sources(lqcd_ctx* c, int s0, int k, const double* b, const doub
 // context x_e = b_e + k D_eo x_o is reconstructed first and, when resid is given,
 // resid[j] = ||b - A x|| / ||b|| of the full system in FP64 (the certificate).
 lqcd_status store_solutions(lqcd_ctx* c, int s0, int k, double* x, int on_device, double* resid = nullptr) {
+    Range nvtx_("solutions from device");
     if (!c->eo) return download(c, c->x_hi_all + (size_t)s0 * c->N, 0, k, x, on_device);
     double2* bf = c->bfull_all + (size_t)s0 * c->Nfull;
     double2* xf = c->xfull_all + (size_t)s0 * c->Nfull;
@@ -783,6 +811,7 @@ constexpr double DEFLATE_GROWTH_MAX = 4.0;
 // correction is then noise that the FP32 gamma5 recursion may not recover from
 // (the general BiCG does). With the guard, rt holds b - A x_hi on return.
 lqcd_status deflate_range(lqcd_ctx* c, int s0, int k, bool precise = false, bool first = false) {
+    Range nvtx_("deflation");
     const int n = c->n_def;
     if (n == 0 || k == 0) return LQCD_OK;
     const bool guard = first && c->p.gamma5;
@@ -857,6 +886,7 @@ lqcd_status refactor(lqcd_ctx* c) {
 // step 2), scaling to unit norm and growing H = U_l^H A U_r and M = U_l^H U_r.
 // work: at least 4*nn Krylov fields (A V', V', A^H W', W').
 lqcd_status grow_space(lqcd_ctx* c, int nn, void* work) {
+    Range nvtx_("eigenspace growth");
     const int n = c->n_def, ld = c->n_def_max;
     nn = std::min(nn, c->n_def_max - n);
     if (nn <= 0) return LQCD_OK;
@@ -1095,6 +1125,7 @@ lqcd_status run_chunk(lqcd_ctx* c, int nslots, int kinds) {
 // the solve out (idle).
 lqcd_status solve_slots(lqcd_ctx* c, int k, int windowed, double tol, bool rec_stop = false, bool precise = false,
                         const int* maxiter = nullptr, bool stab = false) {
+    Range nvtx_("BiCG iterations");
     for (int s = 0; s < c->kmax; ++s) {
         SlotState& st = c->h_state[s];
         memset(&st, 0, sizeof(SlotState));
@@ -1179,6 +1210,7 @@ lqcd_status grow_slot(lqcd_ctx* c, int s, bool ritz_ready = false) {
 
 // After an eigBiCG batch: final Ritz vectors of every slot, appended in slot order.
 lqcd_status grow_from_windows(lqcd_ctx* c, int k) {
+    Range nvtx_("final Ritz vectors");
     c->last_window_valid = 1;
     if (k > 0) {   // final Ritz pairs of every window in one launch (each depends on its window only)
         double2* Yc = c->ritz_all;
@@ -1206,6 +1238,7 @@ lqcd_status status_of(const SlotState& st) {
 
 extern "C" lqcd_status lqcd_solve(lqcd_ctx* c, int k, const double* b, double* x, int on_device, lqcd_mode mode,
                                   lqcd_solve_info* info) {
+    Range nvtx_("lqcd_solve");
     if (!c || k < 0 || (k > 0 && (!b || !x))) return LQCD_ERR_ARG;
     if (mode < LQCD_MODE_AUTO || mode > LQCD_MODE_PLAIN) return LQCD_ERR_ARG;
     if (c->session_busy()) {
@@ -1385,6 +1418,7 @@ extern "C" lqcd_status lqcd_eigspace_set(lqcd_ctx* c, int n, const double* Ur, c
 // ============================================================ Rayleigh-Ritz
 extern "C" lqcd_status lqcd_eigs(lqcd_ctx* c, int* n_inout, double* evals, double* evecs_r, double* evecs_l,
                                  double* resid) {
+    Range nvtx_("Rayleigh-Ritz");
     if (!c || !n_inout || !evals) return LQCD_ERR_ARG;
     const int n = c->n_def;
     if (n == 0) return LQCD_ERR_STATE;
@@ -1717,6 +1751,7 @@ extern "C" lqcd_status lqcd_set_dslash_variant(lqcd_ctx* c, int variant) {
 // Autotuner: time every operator-kernel variant on this lattice with a full
 // batch and keep the fastest (FP32 operator only; FP64 has one shape).
 static lqcd_status autotune(lqcd_ctx* c) {
+    Range nvtx_("autotune operator shapes");
     if (c->eo) return LQCD_OK;   // the even-odd operator and its FP64 residual have one shape each
     {   // FP64 true-residual shape
         double best_ru = 1e300;
@@ -1772,6 +1807,7 @@ static lqcd_status autotune(lqcd_ctx* c) {
 // update, direction update) over k = 1, 2, 4, 8 slots and keep the k with the most
 // right-hand sides per second (ties to the larger k, which needs fewer launches).
 static lqcd_status autotune_batch(lqcd_ctx* c) {
+    Range nvtx_("autotune batch size");
     double best = 0.0;
     int kbest = c->kmax;
     for (int k = 1; k <= c->kmax; k *= 2) {
@@ -1898,6 +1934,7 @@ lqcd_status begin_slot(lqcd_ctx* c, int s, lqcd_mode md, double tol, bool window
 // runs to deftol, is deflated again and then runs to tol (the DefTol restart),
 // exactly as lqcd_solve does.
 lqcd_status admit(lqcd_ctx* c, int s, const lqcd_ctx::Request& req, lqcd_mode md) {
+    Range nvtx_("admit request");
     lqcd_ctx::SlotJob& job = c->jobs[s];
     lqcd_status r = load_sources(c, s, 1, req.b, req.x, req.on_device);
     if (r != LQCD_OK) return r;
@@ -1923,6 +1960,7 @@ lqcd_status admit(lqcd_ctx* c, int s, const lqcd_ctx::Request& req, lqcd_mode md
 // leg of the DefTol restart, or eigenspace growth for an eigBiCG request and
 // the solution back to the caller's buffer.
 lqcd_status retire(lqcd_ctx* c, int s) {
+    Range nvtx_("retire request");
     lqcd_ctx::SlotJob& job = c->jobs[s];
     CK(launch_bicg_finish(c->g, c->links64, c->p.kappa, c->kprec, c->d_state + s, c->d_ptrs + s, 1, c->N, c->stream,
                           c->ru_variant, c->eo ? 1 : 0));
@@ -2002,6 +2040,7 @@ extern "C" lqcd_status lqcd_submit(lqcd_ctx* c, const double* b, double* x, int 
 }
 
 extern "C" lqcd_status lqcd_progress(lqcd_ctx* c, int wait, int* pending) {
+    Range nvtx_("lqcd_progress");
     if (!c) return LQCD_ERR_ARG;
     if (!wait && c->chunk_inflight) {
         cudaError_t q = cudaEventQuery(c->chunk_ev);
