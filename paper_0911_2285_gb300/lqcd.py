@@ -172,6 +172,18 @@ def _ptr(a, n_expected=None):
     return C.c_void_p(a.ctypes.data), 0
 
 
+def _current_cuda_device():
+    """Index of the current CUDA device if torch has initialised CUDA, else None (the
+    context was then created on the CUDA runtime's current device, not known here)."""
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_device()
+    except ImportError:  # pragma: no cover
+        pass
+    return None
+
+
 def _fingerprint(a):
     """Digest of a whole gauge field (shape and every link entry), to refuse an
     eigenspace saved for another field. Hashes the contiguous buffer once per
@@ -230,6 +242,26 @@ class Solver:
         _check(st, "lqcd_eigbicg_init")
         self._h = h
         self.kmax = k_max or 8
+        self._own_stream = not stream
+        self._device = _current_cuda_device()
+
+    def _fields(self, a, c, n_a=None, n_c=None):
+        """Pointers of two fields of one call, both host or both device; device tensors
+        must live on the context's GPU. A context on its private stream does not wait
+        for work queued on torch's current stream, so that work (e.g. the zero fill of
+        an initial guess) is finished first."""
+        pa, da = _ptr(a, n_a)
+        pc, dc = _ptr(c, n_c)
+        if da != dc:
+            raise ValueError("both fields must be host arrays or both device tensors")
+        if da:
+            import torch
+            for t in (a, c):
+                if self._device is not None and t.device.index != self._device:
+                    raise ValueError(f"device tensors must be on cuda:{self._device}, got {t.device}")
+            if self._own_stream:
+                torch.cuda.current_stream(a.device).synchronize()
+        return pa, pc, da
 
     def memory_info(self):
         """``(plan_bytes, window_bytes, windows_attached)``: the fixed device-memory plan,
@@ -282,10 +314,7 @@ class Solver:
         else:
             x = _as_batch(x0, self.n)
             x = x.clone() if hasattr(x, "clone") else x.copy()
-        pb, db = _ptr(b, k * self.n)
-        px, dx = _ptr(x, k * self.n)
-        if db != dx:
-            raise ValueError("b and x must both be host or both be device arrays")
+        pb, px, db = self._fields(b, x, k * self.n, k * self.n)
         infos = (SolveInfo * max(k, 1))()
         st = lib().lqcd_solve(self._h, k, pb, px, db, _MODES[mode] if isinstance(mode, str) else int(mode), infos)
         if raise_on_fail:
@@ -296,10 +325,7 @@ class Solver:
     def submit(self, b, x, mode="auto"):
         """Queue one source; ``x`` holds the initial guess and receives the solution.
         Both arrays must stay alive until :meth:`poll` reports the ticket done."""
-        pb, db = _ptr(b, self.n)
-        px, dx = _ptr(x, self.n)
-        if db != dx:
-            raise ValueError("b and x must both be host or both be device arrays")
+        pb, px, db = self._fields(b, x, self.n, self.n)
         t = C.c_longlong()
         _check(lib().lqcd_submit(self._h, pb, px, db, _MODES[mode] if isinstance(mode, str) else int(mode),
                                  C.byref(t)), "lqcd_submit")
@@ -325,8 +351,9 @@ class Solver:
         b = _as_batch(b, self.n)
         x = _as_batch(x0, self.n)
         x = x.clone() if hasattr(x, "clone") else x.copy()
-        pb, db = _ptr(b)
-        px, dx = _ptr(x)
+        if b.shape != x.shape:
+            raise ValueError("b and x0 must have the same shape")
+        pb, px, db = self._fields(b, x)
         _check(lib().lqcd_deflate(self._h, b.shape[0], pb, px, db), "lqcd_deflate")
         return x
 
@@ -335,8 +362,7 @@ class Solver:
         odd half lattice of an even-odd context."""
         v = _as_batch(v, self.n_space)
         out = _zeros_like(v)
-        pv, dv = _ptr(v)
-        po, do = _ptr(out)
+        pv, po, dv = self._fields(v, out)
         _check(lib().lqcd_apply(self._h, int(dagger), _PREC[precision], v.shape[0], pv, po, dv), "lqcd_apply")
         return out
 

@@ -72,3 +72,23 @@ def test_init_refuses_a_plan_above_the_hbm_budget_without_touching_the_device(li
                  hbm_budget_bytes=8 << 20)
     assert e.value.status == L.ERR_OOM
     assert "budget" in L.last_error()
+
+
+def test_binding_pairs_fields_of_one_kind():
+    """The binding hands the library two fields of one call only when both are host
+    memory or both device memory of the context's GPU (host logic, no context)."""
+    np = pytest.importorskip("numpy")
+    from paper_0911_2285_gb300.lqcd import Solver
+    s = Solver.__new__(Solver)
+    s._own_stream, s._device = True, None
+    a = np.zeros((2, 24), dtype=np.complex128)
+    c = np.ones((2, 24), dtype=np.complex128)
+    pa, pc, dev = s._fields(a, c, 48, 48)
+    assert dev == 0 and pa.value == a.ctypes.data and pc.value == c.ctypes.data
+    with pytest.raises(ValueError):
+        s._fields(a, c, 48, 24)
+    with pytest.raises(TypeError):
+        s._fields(a, c.astype(np.complex64))
+    torch = pytest.importorskip("torch")
+    pa, pc, dev = s._fields(a, torch.zeros(2, 24, dtype=torch.complex128))
+    assert dev == 0
