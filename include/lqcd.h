@@ -28,7 +28,10 @@
  *
  * Memory: the caller owns every buffer it passes.  With on_device = 0 the
  * pointers are host memory (pageable or pinned); with on_device = 1 they are
- * device pointers on the context's GPU, ordered on the context's stream.
+ * device pointers on the context's GPU, ordered on the context's stream
+ * (managed memory is accepted either way).  lqcd_solve, lqcd_submit,
+ * lqcd_deflate and lqcd_apply return LQCD_ERR_ARG, before any copy or launch,
+ * when a buffer's memory kind does not match on_device.
  * The context owns its device copies of the links, the residual windows and
  * the accumulated eigenspace.
  *

@@ -88,6 +88,7 @@ struct lqcd_ctx {
     bool k_auto = false;
     double k_ms[MAX_SLOTS + 1] = {};   // autotuner: ms of one iteration (operator, updates) per batch size
     cudaStream_t stream = nullptr;
+    int device = 0;                 // the CUDA device current at init
     bool own_stream = false;
     std::vector<void*> allocs;
 
@@ -299,6 +300,28 @@ lqcd_status set_ptrs(lqcd_ctx* c) {
     return LQCD_OK;
 }
 
+// A caller's buffer matches on_device: device (or managed) memory of the
+// context's GPU for on_device = 1, host memory (pageable, pinned or managed) for
+// on_device = 0. A host buffer passed as device memory would be read by the
+// kernels, a device buffer passed as host memory by a host copy: both refused.
+bool user_buffer_ok(const lqcd_ctx* c, const void* p, int on_device) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return !on_device;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (on_device) return a.type == cudaMemoryTypeDevice && a.device == c->device;
+    return a.type != cudaMemoryTypeDevice;
+}
+
+lqcd_status check_buffers(const lqcd_ctx* c, const void* a, const void* b, int on_device, const char* where) {
+    if (user_buffer_ok(c, a, on_device) && user_buffer_ok(c, b, on_device)) return LQCD_OK;
+    g_last_error = std::string(where) + (on_device ? ": a buffer is not device memory of the context's GPU"
+                                                   : ": a buffer is device memory but on_device = 0");
+    return LQCD_ERR_ARG;
+}
+
 // Point slot s's V and W at its window (attached) or at its base fields.
 lqcd_status upload_ptrs(lqcd_ctx* c, int s) {
     SlotPtrs& P = c->h_ptrs[s];
@@ -449,6 +472,8 @@ extern "C" lqcd_status lqcd_eigbicg_init(lqcd_ctx** out, const lqcd_params* para
         if (e != cudaSuccess) { set_error("cudaMalloc " #ptr, e); return fail(e == cudaErrorMemoryAllocation ? LQCD_ERR_OOM : LQCD_ERR_CUDA); } \
     } while (0)
 
+    e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) { set_error("cudaGetDevice", e); delete c; return LQCD_ERR_CUDA; }
     if (cuda_stream) {
         c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -779,6 +804,10 @@ extern "C" lqcd_status lqcd_apply(lqcd_ctx* c, int dagger, lqcd_precision prec, 
     if (!c || !in || !out || k < 0) return LQCD_ERR_ARG;
     const int pr = prec == LQCD_MIXED ? 1 : 0;
     if (pr && !c->links32) return LQCD_ERR_ARG;
+    if (k > 0) {
+        lqcd_status s = check_buffers(c, in, out, on_device, "lqcd_apply");
+        if (s != LQCD_OK) return s;
+    }
     // work in chunks of kmax fields: input in x_hi_all / x_lo_all, output in rt_all / win
     for (int j0 = 0; j0 < k; j0 += c->kmax) {
         const int kb = std::min(c->kmax, k - j0);
@@ -1013,6 +1042,10 @@ lqcd_status grow_space(lqcd_ctx* c, int nn, void* work) {
 extern "C" lqcd_status lqcd_deflate(lqcd_ctx* c, int k, const double* b, double* x0, int on_device) {
     if (!c || !b || !x0 || k < 0) return LQCD_ERR_ARG;
     if (c->n_def == 0) return LQCD_ERR_STATE;
+    if (k > 0) {
+        lqcd_status s = check_buffers(c, b, x0, on_device, "lqcd_deflate");
+        if (s != LQCD_OK) return s;
+    }
     for (int j0 = 0; j0 < k; j0 += c->kmax) {
         const int kb = std::min(c->kmax, k - j0);
         lqcd_status s = load_sources(c, 0, kb, b + (size_t)j0 * 2 * c->Nfull, x0 + (size_t)j0 * 2 * c->Nfull,
@@ -1244,6 +1277,10 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx* c, int k, const double* b, double* x
     if (c->session_busy()) {
         g_last_error = "lqcd_solve: requests submitted with lqcd_submit are still in flight";
         return LQCD_ERR_STATE;
+    }
+    if (k > 0) {
+        lqcd_status s = check_buffers(c, b, x, on_device, "lqcd_solve");
+        if (s != LQCD_OK) return s;
     }
     lqcd_status worst = LQCD_OK;
     for (int j0 = 0, kb = 0; j0 < k; j0 += kb) {
@@ -2028,6 +2065,10 @@ extern "C" lqcd_status lqcd_submit(lqcd_ctx* c, const double* b, double* x, int 
                                    long long* ticket) {
     if (!c || !b || !x || !ticket) return LQCD_ERR_ARG;
     if (mode < LQCD_MODE_AUTO || mode > LQCD_MODE_PLAIN) return LQCD_ERR_ARG;
+    {
+        lqcd_status s = check_buffers(c, b, x, on_device ? 1 : 0, "lqcd_submit");
+        if (s != LQCD_OK) return s;
+    }
     lqcd_ctx::Request r;
     r.ticket = c->next_ticket++;
     r.b = b;

@@ -48,6 +48,36 @@ def test_apply_device_pointers_torch():
         assert np.abs(out.cpu().numpy()[0] - ref).max() <= 1e-14 * np.abs(ref).max()
 
 
+def test_buffer_kind_must_match_on_device():
+    """The C ABI refuses a host buffer declared as device memory (the kernels would
+    read it) and a device buffer declared as host memory, before any copy or launch;
+    the context stays usable."""
+    torch = pytest.importorskip("torch")
+    import ctypes as C
+    from paper_0911_2285_gb300 import Solver
+    from paper_0911_2285_gb300.lqcd import ERR_ARG, lib
+    dims = (4, 4, 4, 4)
+    links, op = small_problem(dims)
+    v = random_field(op.n, 3)
+    host_out = np.zeros_like(v)
+    with Solver(links, dims, 0.12, nev=4, m=12, precision="fp64", k_max=1) as s:
+        h = s._h
+        st = lib().lqcd_apply(h, 0, 0, 1, C.c_void_p(v.ctypes.data), C.c_void_p(host_out.ctypes.data), 1)
+        assert st == ERR_ARG
+        tv = torch.from_numpy(v).to("cuda")
+        tout = torch.zeros_like(tv)
+        torch.cuda.synchronize()
+        st = lib().lqcd_apply(h, 0, 0, 1, C.c_void_p(tv.data_ptr()), C.c_void_p(tout.data_ptr()), 0)
+        assert st == ERR_ARG
+        st = lib().lqcd_solve(h, 1, C.c_void_p(v.ctypes.data), C.c_void_p(host_out.ctypes.data), 1, 3, None)
+        assert st == ERR_ARG
+        tk = C.c_longlong()
+        st = lib().lqcd_submit(h, C.c_void_p(tv.data_ptr()), C.c_void_p(host_out.ctypes.data), 1, 3, C.byref(tk))
+        assert st == ERR_ARG
+        ref = op.apply(v)
+        assert np.abs(s.apply(v)[0] - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
 def test_apply_full_size_24x24x24x64_sampled():
     """The largest workload (10.6M unknowns): every site of a random field, FP64 and FP32."""
     from paper_0911_2285_gb300 import Solver
